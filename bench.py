@@ -1,0 +1,330 @@
+#!/usr/bin/env python
+"""USBS solves/sec on GB300: MaxCut SDP on the 1000 x 1000 toroidal grid.
+
+Workload (one "step"): a cold-start USBS solve of MaxCut on the 1000 x 1000 torus
+(n = 1,000,000 vertices, 2,000,000 edges, weights +-1 with probability 1/2, seed 0)
+with a rank-16 Nystrom sketch (Gaussian Psi, seed 1), k_c = 8, mixed precision (FP32
+bulk, FP64 k-sized work), until both the relative gap and the relative infeasibility
+are <= 1e-3 (scaled units, the paper's gates).  Inputs are synthetic; the problem data
+(~100 MB) and the Lanczos basis (~290 MB) exceed the 126 MB L2, so no flush is needed.
+
+`value` times usbs_solve with the problem already resident in HBM; `e2e` times, per
+step, usbs_create from pinned host arrays (H2D inside), the solve, and the read-back of
+y and the sketch.  Several GPUs run independent replicas (no collective).
+
+--impl reference times the FP64 CPU oracle on a bounded sample (see cpu_baseline).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "solves/sec at gap<=1e-3: served vs plain (same GPU); Lanczos HBM GB/s; p99"
+UNIT = "solves/sec"
+TOL = 1e-3
+SIDE, R_SKETCH = 1000, 16
+WORKLOAD = "maxcut_torus_1000x1000_pm1_r16_mixed"
+
+
+def peaks():
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def make_problem(side=SIDE):
+    from paper_2312_11801_gb300 import instances as I
+    prob = I.maxcut_torus(side, seed=0, signed=True)
+    psi = I.gaussian_psi(prob.n, R_SKETCH, seed=1)
+    return prob, psi
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        sm = [float(r[0]) for r in self.rows if len(r) >= 7 and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) >= 7 and r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows if len(r) >= 7
+                          for i in range(4) if r[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, x):
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on a bounded sample
+# ---------------------------------------------------------------------------------------
+SAMPLE_SIDE = 72         # a 72 x 72 torus of the same family (n = 5,184, block Lanczos path)
+SAMPLE_ITERS = 2
+
+
+def oracle_sample(gpu_iters_per_solve, budget_s=40.0):
+    """Oracle seconds per USBS iteration on the sample, scaled to the full workload.
+
+    The sample runs the oracle (as it stands: block Lanczos to a 1e-6 residual for
+    n > 4096, FP64 throughout) on a 72 x 72 torus with the same weights law and sketch
+    rank, for up to SAMPLE_ITERS iterations after its cold start.  Every step of an
+    iteration is linear in n for these graphs, so seconds per iteration are scaled by
+    1e6 / 5184; solves/sec divides by the iterations the GPU solve needed.
+    """
+    from paper_2312_11801_gb300 import instances as I
+    from oracle.usbs import USBSOracle
+    prob = I.maxcut_torus(SAMPLE_SIDE, seed=0, signed=True)
+    psi = I.gaussian_psi(prob.n, R_SKETCH, seed=1)
+    o = USBSOracle(prob, k=8, psi=psi, eig_tol=1e-6)
+    t0 = time.perf_counter()
+    o.cold_start()
+    t1 = time.perf_counter()
+    done = 0
+    while done < SAMPLE_ITERS and time.perf_counter() - t1 < budget_s:
+        o.step()
+        done += 1
+    t2 = time.perf_counter()
+    per_iter = (t2 - t1) / max(done, 1)
+    scale = (SIDE * SIDE) / prob.n
+    per_solve = scale * (per_iter * max(gpu_iters_per_solve, 1) + (t1 - t0))
+    try:
+        import threadpoolctl
+        cores = max(info.get("num_threads", 1) for info in threadpoolctl.threadpool_info()) or 1
+    except Exception:
+        cores = os.cpu_count()
+    return {"value": 1.0 / per_solve, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"FP64 oracle: cold start + {done} USBS iterations on the "
+                       f"{SAMPLE_SIDE}x{SAMPLE_SIDE} +-1 torus (n={prob.n}, r=16), "
+                       f"{per_iter:.3f} s/iteration, scaled x{scale:.0f} in n and by "
+                       f"{gpu_iters_per_solve} iterations per solve"),
+            "seconds": t2 - t0}
+
+
+# ---------------------------------------------------------------------------------------
+def run_ours(args, world, rank, local, pg):
+    import torch
+    from paper_2312_11801_gb300 import build as B
+    B.build()
+    from paper_2312_11801_gb300 import usbs as U
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    prob, psi = make_problem(args.side)
+    stream = torch.cuda.Stream(device=dev)
+    params = dict(r=R_SKETCH, precision=U.PRECISION_MIXED, stream=stream, max_iters=args.max_iters)
+    ctx = U.usbs_create(prob, psi=psi, **params)
+
+    # warm-up solves (also give the iteration count of one solve)
+    warm = []
+    for _ in range(args.warmup):
+        warm.append(U.usbs_solve(ctx, warm_start=False, tol=TOL))
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    U.usbs_profile(ctx, True)
+    launches0 = U.usbs_launch_count(ctx)
+    results = []
+    barrier(pg)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        results.append(U.usbs_solve(ctx, warm_start=False, tol=TOL))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(pg)
+    elapsed = e0.elapsed_time(e1) / 1e3
+    launches = U.usbs_launch_count(ctx) - launches0
+    stats = U.usbs_kernel_stats(ctx)
+    U.usbs_profile(ctx, False)
+    clk = clocks.stop()
+    elapsed_max = max_over_ranks(pg, elapsed)
+
+    # end to end through the C ABI from pinned host arrays
+    arrays = U._problem_arrays(prob)
+    pinned = []
+    for a in list(arrays) + [np.ascontiguousarray(psi, np.float32)]:
+        t = torch.from_numpy(a).pin_memory()
+        pinned.append(t.numpy())
+    h2d = sum(a.nbytes for a in pinned)
+    d2h = 8 * prob.m + 4 * prob.n * R_SKETCH + 16
+    from paper_2312_11801_gb300.instances import Problem
+    pprob = Problem(prob.n, pinned[0], pinned[1], pinned[2], pinned[3], pinned[4], pinned[5],
+                    pinned[6], pinned[7], pinned[8], prob.trace, prob.name)
+    barrier(pg)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_iters = []
+    for _ in range(args.e2e_steps):
+        c2 = U.usbs_create(pprob, psi=pinned[9], **params)
+        res = U.usbs_solve(c2, warm_start=False, tol=TOL)
+        U.usbs_get_dual(c2)
+        U.usbs_get_sketch(c2)
+        c2.close()
+        e2e_iters.append(res["iters"])
+    torch.cuda.synchronize()
+    e2e_elapsed = max_over_ranks(pg, time.perf_counter() - t0)
+
+    iters = [r["iters"] for r in results]
+    conv = all(r["converged"] for r in results)
+    hbm, peak_src = peaks()
+    # roofline of the dominant bulk kernel kind (largest device time)
+    bulk = {k: v for k, v in stats.items() if v[2] > 0}
+    dom = max(bulk, key=lambda k: bulk[k][0])
+    ms, nl, by = bulk[dom]
+    achieved = (by / nl) / ((ms / 1e3) / nl) / 1e9 if ms > 0 else 0.0
+    spmm_ms, spmm_n, spmm_b = stats["spmm"]
+    spmm_gbs = spmm_b / (spmm_ms / 1e3) / 1e9 if spmm_ms > 0 else 0.0
+    total_ms = sum(v[0] for v in stats.values())
+    line = {
+        "metric": METRIC, "value": world * args.steps / elapsed_max, "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * elapsed_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": prob.n, "edges": 2 * SIDE * SIDE, "weights": "+-1",
+                   "r": R_SKETCH, "k_c": 8, "rho": 0.01, "beta": 0.25, "tol": TOL,
+                   "precision": "mixed: FP32 bulk, FP64 k-sized", "parallelism": f"replicas{world}",
+                   "l2": "inputs and basis larger than L2 (no flush)",
+                   "iters_per_solve": iters, "converged": conv},
+        "e2e": {"value": world * args.e2e_steps / e2e_elapsed, "unit": UNIT,
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
+                     "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": None, "peak_source": peak_src},
+        "lanczos_spmm": {"achieved_gbs": spmm_gbs, "frac": spmm_gbs / hbm, "launches": spmm_n,
+                         "avg_us": 1e3 * spmm_ms / max(spmm_n, 1),
+                         "bytes_per_launch": spmm_b / max(spmm_n, 1)},
+        "kernel_share": {k: round(v[0] / total_ms, 4) for k, v in stats.items() if total_ms > 0},
+        "clocks": clk,
+    }
+    if rank == 0:
+        if not args.no_cpu:
+            line["cpu_baseline"] = oracle_sample(int(statistics.median(iters)))
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def run_reference(args, world, rank):
+    """The oracle arm: each step is the bounded oracle sample of run_ours's workload."""
+    if rank != 0:
+        return
+    gpu_iters = args.ref_iters
+    vals = []
+    for _ in range(args.warmup):
+        oracle_sample(gpu_iters, budget_s=20.0)
+    t0 = time.perf_counter()
+    last = None
+    for _ in range(args.steps):
+        last = oracle_sample(gpu_iters, budget_s=20.0)
+        vals.append(last["value"])
+    wall = time.perf_counter() - t0
+    value = statistics.median(vals)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": WORKLOAD, "n": SIDE * SIDE, "r": R_SKETCH, "tol": TOL},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
+                         "sample": last["sample"]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--side", type=int, default=SIDE)
+    ap.add_argument("--max-iters", type=int, default=2000)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ref-iters", type=int, default=100,
+                    help="iterations per solve used to scale the reference arm's sample")
+    args = ap.parse_args()
+    world, rank, local, pg = dist_setup() if args.impl == "ours" else (
+        int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0, None)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local, pg)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,271 @@
+/*
+ * usbs.h -- C ABI of libusbs, the GB300 (sm_103a) hot path of USBS, the unified
+ * spectral bundle method with sketching of Angell & McCallum (arXiv 2312.11801).
+ *
+ * Problem (Sec. 2.1, programs (P) and (D)):
+ *     maximise <C, X>  s.t.  <A_c, X> = b_c (c not in I),  <A_c, X> <= b_c (c in I),  X PSD
+ * with C symmetric n x n and A_1..A_m symmetric.  USBS minimises the penalised dual
+ * f(y) = alpha [lambda_max(C - A*(y))]_+ + <b, y> over y_I >= 0 (eq. pen-D) by the
+ * proximal bundle iteration of Algorithm 1 (Sec. 3), keeping the primal implicit
+ * (<C, Xbar>, tr Xbar, A Xbar; App. C) and, when r > 0, a Nystrom sketch P = Xbar Psi
+ * (Sec. 4).
+ *
+ * Conventions shared by every call
+ *  - Return value: USBS_OK (0) or a negative USBS_E* code.  No exception crosses the
+ *    ABI.  usbs_last_error(ctx) gives a message for the last failing call on ctx
+ *    (usbs_last_error(NULL) for failures of usbs_create itself).
+ *  - Indices are 0-based.  Matrices are row-major.
+ *  - Host pointers are read during the call only; the library copies what it keeps.
+ *  - The library owns all device memory it allocates; it is released by usbs_destroy.
+ *  - All work is queued on usbs_params.stream (a cudaStream_t; NULL = a stream the
+ *    context creates).  Calls that return host data synchronise that stream.
+ *  - A context is not thread-safe: one host thread at a time per context.
+ *  - Units: inputs and outputs are in the units of the problem as given.  Internally
+ *    the problem is scaled so that ||C||_F = tr(X*) = 1 and alpha = 2 (App. E);
+ *    the stopping gates are evaluated in those scaled units, as in the paper.
+ */
+#ifndef USBS_H
+#define USBS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define USBS_ABI_VERSION 1
+
+/* status codes */
+#define USBS_OK          0
+#define USBS_EINVAL     -1   /* bad argument: sizes, index ranges, NULL where required */
+#define USBS_ENOMEM     -2   /* device allocation failed */
+#define USBS_ECUDA      -3   /* a CUDA runtime call failed (message has the CUDA error) */
+#define USBS_ETIMEOUT   -4   /* a bounded device-side wait ran out */
+#define USBS_ENOTCONV   -5   /* usbs_solve hit max_iters before both gates passed */
+#define USBS_EBUSY      -6   /* server or batch has no free slot / budget */
+#define USBS_ENUMERIC   -7   /* non-finite value in an FP64 reduction or the IPM */
+
+/* arithmetic of the bulk (n-sized) work; k-sized work is FP64 in both modes */
+#define USBS_PRECISION_FP64   0  /* SpMM, Lanczos basis, V, sketch in FP64 */
+#define USBS_PRECISION_MIXED  1  /* SpMM, reorthogonalisation, V, sketch in FP32 */
+
+typedef struct usbs_ctx usbs_ctx;
+
+typedef struct usbs_params {
+  double alpha;            /* trace bound after scaling; 0 = 2 (App. E) */
+  double rho;              /* proximal parameter (eq. proposal_step); default 0.01 */
+  double beta;             /* descent fraction (eq. descent_cond); default 0.25 */
+  int    k_c;              /* current eigenvectors kept in V, 1..8; default 8 */
+  int    k_p;              /* past-information columns; only 0 is supported */
+  int    r;                /* sketch rank (Sec. 4); 0 = no sketch */
+  int    precision;        /* USBS_PRECISION_*; default MIXED */
+  int    lanczos_basis;    /* block Lanczos basis columns J (multiple of 16, <= 64) */
+  int    lanczos_restarts; /* Rayleigh-Ritz cycles per eigen solve (App. E: 10) */
+  double lanczos_tol;      /* stop when the top-k_c Ritz residuals <= tol * |theta|_max */
+  double ipm_mu_tol;       /* IPM stops once mu < ipm_mu_tol (App. B.1: 1e-7) */
+  int    ipm_max_iter;     /* Newton steps per IPM call; default 100 */
+  int    max_alt;          /* alternating-maximisation passes (eq. small_quad_sdp); 50 */
+  double alt_tol;          /* stop alternation when ||d nu|| <= alt_tol (1 + ||b||) */
+  double trace_hint;       /* tr(X*) before scaling; 0 = derive from diag equalities */
+  int    max_iters;        /* iteration cap of usbs_solve; default 1000 */
+  uint64_t seed;           /* seeds the random start/deflation vectors of Lanczos */
+  void*  stream;           /* cudaStream_t to run on; NULL = own stream */
+  int    device;           /* CUDA device ordinal; -1 = current device */
+} usbs_params;
+
+typedef struct usbs_eig_info {
+  int    cycles;           /* Rayleigh-Ritz cycles run */
+  int    matvecs;          /* single-vector products with C - A*(y) (block size x SpMMs) */
+  int    converged;        /* 1 if every top-k_c residual met lanczos_tol */
+  double max_residual;     /* max over top k_c of ||M v - theta v|| (scaled units) */
+} usbs_eig_info;
+
+typedef struct usbs_step_info {
+  int    t;                /* iteration index after the step */
+  int    descent;          /* 1 = descent step, 0 = null step (Algorithm 1) */
+  int    n_alt;            /* alternating-maximisation passes used */
+  int    ipm_iters;        /* Newton steps summed over the passes */
+  int    matvecs;          /* Lanczos products at the candidate */
+  double f_y;              /* f(y_{t+1}), scaled units */
+  double f_cand;           /* f(y~_{t+1}) */
+  double f_hat;            /* model value f^_t(y~_{t+1}) */
+  double lambda_max;       /* lambda_max(C - A*(y~_{t+1})), scaled */
+  double cx;               /* <C, X_{t+1}>, scaled */
+  double trx;              /* tr X_{t+1}, scaled */
+  double eta;              /* weight on Xbar_t in X_{t+1} */
+  double relgap;           /* |f(y) - <C,X>| / (1 + |<C,X>|), scaled (App. E) */
+  double relinf;           /* dist(A X, K) / (1 + ||b||), scaled (eq. relative_error_tol) */
+  double relinf_max;       /* ||A X - proj_K(A X)||_inf, scaled */
+  double objective;        /* <C, X_{t+1}> in the units of the given problem */
+  double dual_bound;       /* f(y_{t+1}) in the units of the given problem */
+} usbs_step_info;
+
+typedef struct usbs_result {
+  int    iters;            /* iterations run by this call */
+  int    converged;        /* both gates <= tol */
+  int    descent_steps;
+  long long matvecs;       /* total Lanczos single-vector products */
+  usbs_step_info last;     /* diagnostics of the last iteration */
+} usbs_result;
+
+/* Fill *p with the defaults listed above. */
+void usbs_params_default(usbs_params* p);
+
+/* Version of this ABI (USBS_ABI_VERSION). */
+int usbs_abi_version(void);
+
+/* Message of the last failure on ctx (NULL ctx: last failure of usbs_create).
+ * The string stays valid until the next call on ctx. */
+const char* usbs_last_error(const usbs_ctx* ctx);
+
+/*
+ * usbs_create -- copy one problem (C, A, b, I) of Sec. 2.1 to the device and set the
+ * state to the cold start y_0 = 0, Xbar_0 = 0 (the first solve computes V_0).
+ *
+ *  n        : order of C and X (n >= 24).
+ *  C_rowptr : n+1 int64, C_col : nnz int32, C_val : nnz FP64.  C as CSR with BOTH
+ *             triangles; diagonal entries allowed; duplicates are summed.
+ *  m        : number of constraints; nnzA entries (A_con[e], A_i[e], A_j[e], A_val[e])
+ *             each add A_val[e] * X_ij to <A_con[e], X>.  For i != j the entry stands for
+ *             the symmetric matrix (v/2)(e_i e_j^T + e_j e_i^T); i > j is swapped.
+ *  b        : m FP64.  is_ineq : m uint8, nonzero = row is <A_c, X> <= b_c.
+ *  Psi      : n x r FP32 row-major sketch test matrix (Sec. 4), required iff p->r > 0.
+ *  p        : parameters (NULL = defaults).
+ * Errors: USBS_EINVAL (sizes, index ranges, r > 0 without Psi, n < 24, k_p != 0,
+ * unknown trace), USBS_ENOMEM, USBS_ECUDA.  *out is NULL on failure.
+ */
+int usbs_create(usbs_ctx** out, int64_t n, const int64_t* C_rowptr, const int32_t* C_col,
+                const double* C_val, int64_t m, int64_t nnzA, const int32_t* A_con,
+                const int32_t* A_i, const int32_t* A_j, const double* A_val,
+                const double* b, const uint8_t* is_ineq, const float* Psi,
+                const usbs_params* p);
+
+/* Release every device allocation of ctx.  NULL is allowed. */
+int usbs_destroy(usbs_ctx* ctx);
+
+/*
+ * usbs_extreme_eigs -- top-k_c eigenpairs of the dual slack matrix C - A*(y)
+ * (Sec. 3: the cost of each f evaluation; App. E: thick-restart Lanczos), by block
+ * Lanczos with classical Gram-Schmidt reorthogonalisation (two passes) and thick
+ * restart.  Scaled units: the matrix is (C - A*(y_o)) / ||C||_F for y_o given in the
+ * problem's units.
+ *  y      : m FP64 host, in the problem's units; NULL = the context's current y.
+ *  kc     : 1..k_c eigenpairs wanted.
+ *  evals  : kc FP64 host, descending, scaled units (multiply by ||C||_F to unscale).
+ *  evecs  : n x kc FP64 host row-major orthonormal eigenvectors, or NULL.
+ *  info   : optional.
+ * The context's V is not changed.
+ */
+int usbs_extreme_eigs(usbs_ctx* ctx, const double* y, int kc, double* evals,
+                      double* evecs, usbs_eig_info* info);
+
+/* One iteration of Algorithm 1 (lines 4-11).  If the context has no iterate yet the
+ * cold start (y_0 = 0, Xbar_0 = 0, V_0 = top eigenvectors of C) is made first. */
+int usbs_step(usbs_ctx* ctx, usbs_step_info* info);
+
+/*
+ * usbs_solve -- iterate until relgap <= tol and relinf <= tol (App. E gates, scaled
+ * units) or max_iters.  warm_start = 0 restarts from the cold start; 1 continues from
+ * the current state (after usbs_set_state, usbs_grow or earlier steps).
+ * Returns USBS_OK when converged, USBS_ENOTCONV at the cap (out is filled either way).
+ */
+int usbs_solve(usbs_ctx* ctx, int warm_start, double tol, usbs_result* out);
+
+/* Sketch and implicit primal (Sec. 4, App. C), in the problem's units:
+ *  P       : n x r FP32 host, X Psi (may be NULL),  Psi : n x r FP32 host (may be NULL),
+ *  scalars : 2 FP64 host {<C, Xbar>, tr Xbar} (may be NULL). */
+int usbs_get_sketch(usbs_ctx* ctx, float* P, float* Psi, double* scalars);
+
+/* Current dual iterate y_t (m FP64 host), problem units. */
+int usbs_get_dual(usbs_ctx* ctx, double* y);
+
+/* Current primal constraint values A Xbar (m FP64 host), problem units. */
+int usbs_get_primal_constraints(usbs_ctx* ctx, double* ax);
+
+/*
+ * Complete iterate state (USBS has no iteration-dependent parameters, Sec. 3, so this
+ * is a checkpoint and the warm-start input).  Layout of the FP64 host buffer, problem
+ * units: [y (m), A Xbar (m), <C,Xbar>, tr Xbar, f(y), V (n*k_c row-major), P (n*r)].
+ * usbs_state_size gives its length in doubles.
+ */
+int64_t usbs_state_size(const usbs_ctx* ctx);
+int usbs_get_state(usbs_ctx* ctx, double* state);
+int usbs_set_state(usbs_ctx* ctx, const double* state);
+
+/*
+ * usbs_grow -- warm start of a grown instance (Sec. 5.1: pad the smaller solution with
+ * zeros and rescale).  The new problem must keep the old vertices 0..n_old-1 and
+ * constraints 0..m_old-1 in place.  y, A Xbar, tr Xbar and P are unscaled with the old
+ * scaling, zero-padded, and rescaled with the new one; <C, Xbar> adds the change of C
+ * on old-old entries when that change is diagonal and each changed X_ii is fixed by a
+ * one-entry constraint (MaxCut growth), otherwise the implicit primal restarts at 0.
+ * V is padded with zero rows.  Psi_new (n_new x r) must extend the old Psi.
+ * Arguments after ctx_old are those of usbs_create for the new problem.
+ */
+int usbs_grow(usbs_ctx* ctx_old, usbs_ctx** out, int64_t n, const int64_t* C_rowptr,
+              const int32_t* C_col, const double* C_val, int64_t m, int64_t nnzA,
+              const int32_t* A_con, const int32_t* A_i, const int32_t* A_j,
+              const double* A_val, const double* b, const uint8_t* is_ineq,
+              const float* Psi_new);
+
+/* ---------------------------------------------------------------------------------
+ * Single-operation entry points on device buffers (the rows of one iteration run
+ * alone, for testing and composition).  All pointers are DEVICE pointers; the
+ * operation is queued on the context's stream and the call does not synchronise.
+ * Precision of T-typed buffers follows the context: float (MIXED) or double (FP64).
+ * --------------------------------------------------------------------------------- */
+
+/* Y = (C - A*(y)) X / ||C||_F for X, Y n x 8 row-major (T); y is m FP64 in scaled
+ * units, i.e. the problem's y divided by ||C||_F (usbs_scaling).  The operator of
+ * eq. pen-D. */
+int usbs_op_matmul(usbs_ctx* ctx, const double* y_scaled_dev, const void* X_dev,
+                   void* Y_dev);
+
+/* z = A(V S V^T) (App. C): V n x k_c (T, row-major, k_c columns), S k_c x k_c FP64
+ * row-major, z m FP64; scaled operator, so z is in the units of A. */
+int usbs_op_constraint_eval(usbs_ctx* ctx, const void* V_dev, const double* S_dev,
+                            double* z_dev);
+
+/* Sketch update of Sec. 4 with k_p = 0: P <- eta P + V (S (V^T Psi)), V n x k_c (T),
+ * S k_c x k_c FP64, P and Psi n x r FP32.  eta is a host scalar. */
+int usbs_op_sketch_update(usbs_ctx* ctx, const void* V_dev, const double* S_dev,
+                          const float* Psi_dev, float* P_dev, double eta);
+
+/* ---------------------------------------------------------------------------------
+ * Measurement.  With profiling on, every kernel launch of the context is bracketed by
+ * two CUDA events on its stream and the elapsed device time is added to one of the
+ * kinds below (the events add a few microseconds of host time per launch).
+ * --------------------------------------------------------------------------------- */
+#define USBS_KIND_SPMM      0  /* (C - A*(y)) X, the Lanczos matvec */
+#define USBS_KIND_REORTH    1  /* Gram-Schmidt projections, block update, Cholesky-QR apply */
+#define USBS_KIND_RESTART   2  /* thick-restart and Ritz-vector products Q Y */
+#define USBS_KIND_CONSTR    3  /* per-constraint kernels: G^T G, A(V S V^T), alternation */
+#define USBS_KIND_SMALL     4  /* one-CTA FP64 kernels: Ritz, IPM, Cholesky, model value */
+#define USBS_KIND_REDUCE    5  /* cross-CTA reductions */
+#define USBS_KIND_SKETCH    6  /* V^T Psi and the sketch update */
+#define USBS_KIND_SETUP     7  /* operator set-up for a new y */
+#define USBS_NUM_KINDS      8
+
+/* Turn event timing on (1) or off (0); turning it on clears the totals. */
+int usbs_profile(usbs_ctx* ctx, int on);
+/* Device time (ms), launch count and algorithmic bytes (every input of a launch read
+ * once, every output written once; 0 for the one-CTA kinds) of one kind since profiling
+ * was turned on.  Synchronises the stream.  Any output pointer may be NULL. */
+int usbs_kernel_stats(usbs_ctx* ctx, int kind, double* total_ms, long long* launches,
+                      double* bytes);
+/* Kernels this context has launched since usbs_create (profiling on or off). */
+long long usbs_launch_count(const usbs_ctx* ctx);
+
+/* Scaling of the problem: c = ||C||_F and tau = tr(X*) (App. E). */
+int usbs_scaling(const usbs_ctx* ctx, double* c_scale, double* tau);
+
+/* Sizes the context was built with: n, m, k_c, r, precision, J. */
+int usbs_dims(const usbs_ctx* ctx, int64_t* n, int64_t* m, int* k_c, int* r,
+              int* precision, int* basis);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* USBS_H */

@@ -1,0 +1,52 @@
+"""Write tests/golden/oracle_solves.json: FP64 oracle solves of the small parity cases.
+
+Calls only oracle/ and the input generators.  Usage:
+    python tests/golden/make_oracle_golden.py [name ...]
+"""
+import json
+import math
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+from oracle.usbs import USBSOracle  # noqa: E402
+from paper_2312_11801_gb300 import instances as I  # noqa: E402
+
+# name -> (builder, oracle kwargs, tol, max_iters)
+CASES = {
+    # Erdos-Renyi MaxCut, n = 800, average degree 6, unit weights, seed 0; k = 8
+    "er800_d6_s0": (lambda: I.maxcut_er(800, 6.0, 0), dict(k=8), 1e-4, 5000),
+    # same graph family, smaller, for the per-iteration trajectory test
+    "er120_d6_s3": (lambda: I.maxcut_er(120, 6.0, 3), dict(k=8), 1e-4, 3000),
+    # clustering SDP with equality and inequality rows
+    "clust200_e800_s1": (lambda: I.clustering_sdp(200, 800, 1), dict(k=8), 1e-4, 3000),
+}
+
+
+def run(name):
+    build, kw, tol, iters = CASES[name]
+    prob = build()
+    o = USBSOracle(prob, **kw)
+    t0 = time.time()
+    hist = o.solve(tol=tol, max_iters=iters)
+    last = hist[-1]
+    return {
+        "name": name, "n": prob.n, "m": prob.m, "tol": tol, "iters": len(hist),
+        "converged": bool(last["relgap"] <= tol and last["relinf"] <= tol),
+        "objective": o.objective(), "dual_bound": o.dual_bound(),
+        "cx_scaled": o.state.cx, "f_scaled": o.state.f_y,
+        "relgap": last["relgap"], "relinf": last["relinf"],
+        "c_scale": o.sp.c_scale, "tau": o.sp.tau, "seconds": time.time() - t0,
+    }
+
+
+if __name__ == "__main__":
+    path = os.path.join(HERE, "oracle_solves.json")
+    data = json.load(open(path)) if os.path.exists(path) else {}
+    for name in (sys.argv[1:] or list(CASES)):
+        data[name] = run(name)
+        print(json.dumps(data[name]), flush=True)
+        json.dump(data, open(path, "w"), indent=1, sort_keys=True)

@@ -1,0 +1,94 @@
+"""USBS iterations and solves through the C ABI against the FP64 oracle and closed forms."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle.usbs import USBSOracle
+from paper_2312_11801_gb300 import instances as I
+from tests._graphs import named_graph
+from tests.gpu_util import gpu_modules
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def mods():
+    return gpu_modules()
+
+
+def _golden():
+    return json.load(open(os.path.join(HERE, "golden", "oracle_solves.json")))
+
+
+def test_step_trajectory_matches_oracle_fp64(mods):
+    """Per-iteration f(y), <C,X>, tr X, lambda_max and descent flags of Algorithm 1."""
+    torch, U = mods
+    prob = I.maxcut_er(120, 6.0, 3)
+    ora = USBSOracle(prob, k=8)
+    ora.cold_start()
+    with U.usbs_create(prob, precision=0, lanczos_restarts=300, lanczos_tol=1e-12) as ctx:
+        for t in range(12):
+            g = U.usbs_step(ctx)
+            o = ora.step()
+            assert g["descent"] == int(o["descent"]), t
+            for key_g, key_o in [("f_y", "f_y"), ("cx", "cx"), ("trx", "trX"),
+                                 ("lambda_max", "lambda_max"), ("f_hat", "f_hat")]:
+                assert abs(g[key_g] - o[key_o]) <= 1e-6 * (1 + abs(o[key_o])), (t, key_g, g[key_g], o[key_o])
+
+
+def test_step_trajectory_with_inequalities_fp64(mods):
+    """Alternating maximisation (I not empty): same iterates as the oracle."""
+    torch, U = mods
+    prob = I.clustering_sdp(200, 800, 1)
+    ora = USBSOracle(prob, k=8)
+    ora.cold_start()
+    with U.usbs_create(prob, precision=0, lanczos_restarts=300, lanczos_tol=1e-12) as ctx:
+        for t in range(6):
+            g = U.usbs_step(ctx)
+            o = ora.step()
+            assert g["n_alt"] == o["n_alt"], t
+            assert g["descent"] == int(o["descent"]), t
+            for key_g, key_o in [("f_y", "f_y"), ("cx", "cx"), ("trx", "trX"), ("relinf", "relinf")]:
+                assert abs(g[key_g] - o[key_o]) <= 1e-6 * (1 + abs(o[key_o])), (t, key_g, g[key_g], o[key_o])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("name", ["er800_d6_s0", "clust200_e800_s1"])
+def test_solve_matches_oracle(mods, name, precision):
+    """Both gates <= 1e-3 and <C, X> within 1e-3 (scaled, 1 + |.| denominator) of the
+    oracle's solve at 1e-4."""
+    torch, U = mods
+    gold = _golden()[name]
+    prob = {"er800_d6_s0": lambda: I.maxcut_er(800, 6.0, 0),
+            "clust200_e800_s1": lambda: I.clustering_sdp(200, 800, 1)}[name]()
+    with U.usbs_create(prob, precision=precision, max_iters=5000) as ctx:
+        res = U.usbs_solve(ctx, tol=1e-3)
+    last = res["last"]
+    assert res["converged"], res
+    assert last["relgap"] <= 1e-3 and last["relinf"] <= 1e-3
+    assert abs(last["cx"] - gold["cx_scaled"]) <= 1e-3 * (1 + abs(gold["cx_scaled"]))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("name,value", [
+    ("K24", 24 * 24 / 4), ("C25", 12.5 * (1 + math.cos(math.pi / 25))), ("torus8", 128.0)])
+def test_closed_form_maxcut(mods, name, value, precision):
+    torch, U = mods
+    if name == "torus8":
+        prob = I.maxcut_torus(8, signed=False)       # bipartite: SDP = |E| = 128
+    else:
+        n, i, j, w = named_graph(name)
+        prob = I.maxcut_from_edges(n, i, j, w, name=name)
+    with U.usbs_create(prob, precision=precision, max_iters=3000, rho=0.1,
+                       ipm_mu_tol=1e-10, lanczos_restarts=50) as ctx:
+        res = U.usbs_solve(ctx, tol=1e-5)
+    last = res["last"]
+    slack = 1.01 * max(last["relgap"], 1e-5) * (1 + abs(last["cx"])) * prob.n * 1.0
+    c_scale = float(np.sqrt(np.sum(prob.C_val ** 2)))
+    slack *= c_scale
+    assert last["dual_bound"] >= value * (1 - (1e-9 if precision == 0 else 1e-5))
+    assert abs(last["objective"] - value) <= max(slack, 2e-4 * value), (last, value)
