@@ -257,6 +257,32 @@ int usbs_kernel_stats(usbs_ctx* ctx, int kind, double* total_ms, long long* laun
 /* Kernels this context has launched since usbs_create (profiling on or off). */
 long long usbs_launch_count(const usbs_ctx* ctx);
 
+/*
+ * usbs_sketch_update_static -- the sketch update of usbs_op_sketch_update,
+ * P <- eta P + V (S (V^T Psi)), without a context and without allocating anything.
+ * The paper has no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc, for example a serving process that has handed all of HBM to its own
+ * memory pool up front, or code that must not take the device-wide synchronisation
+ * that cudaMalloc and cudaFree may cause while other work is in flight.
+ *
+ *  n   : rows (1 <= n < 2^31).   r : sketch rank, 1 <= r <= 32 (USBS_EINVAL beyond).
+ *  V_dev   : n x 8 FP32 row-major (columns past k_c zero), device.
+ *  S_dev   : 8 x 8 FP64 row-major, device.
+ *  Psi_dev : n x r FP32 row-major, device.   P_dev : n x r FP32, updated in place.
+ *  stream  : cudaStream_t to run on (NULL = the legacy default stream).
+ * The call only queues work; it does not synchronise.  Returns USBS_OK, USBS_EINVAL
+ * or USBS_ECUDA (no message is recorded).
+ * Its scratch is one static device array of 264,192 bytes (partial sums of V^T Psi and
+ * their total), which every GPU that loads the library holds until the process exits.
+ * The first call on a device looks the array's address up (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  All calls on a
+ * device share the array and it keeps the last call's contents; each call writes every
+ * scratch entry it reads, so nothing needs clearing, but calls that overlap on the GPU
+ * (different streams, or different host threads) race on it and must be serialised.
+ */
+int usbs_sketch_update_static(int64_t n, int r, const float* V_dev, const double* S_dev,
+                              const float* Psi_dev, float* P_dev, double eta, void* stream);
+
 /* Scaling of the problem: c = ||C||_F and tau = tr(X*) (App. E). */
 int usbs_scaling(const usbs_ctx* ctx, double* c_scale, double* tau);
 

@@ -91,6 +91,8 @@ SIGNATURES = [
     ("usbs_op_matmul", ctypes.c_int, [_P, _P, _P, _P]),
     ("usbs_op_constraint_eval", ctypes.c_int, [_P, _P, _P, _P]),
     ("usbs_op_sketch_update", ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_double]),
+    ("usbs_sketch_update_static", ctypes.c_int, [ctypes.c_int64, ctypes.c_int, _P, _P, _P, _P,
+                                                 ctypes.c_double, _P]),
     ("usbs_profile", ctypes.c_int, [_P, ctypes.c_int]),
     ("usbs_kernel_stats", ctypes.c_int, [_P, ctypes.c_int, _D, ctypes.POINTER(ctypes.c_longlong), _D]),
     ("usbs_launch_count", ctypes.c_longlong, [_P]),
@@ -338,3 +340,12 @@ def usbs_kernel_stats(ctx):
 
 def usbs_launch_count(ctx):
     return int(load().usbs_launch_count(ctx.ptr))
+
+
+def usbs_sketch_update_static(n, r, V_dev, S_dev, Psi_dev, P_dev, eta, stream=None):
+    """Context-free sketch update that allocates nothing (see include/usbs.h)."""
+    st = None
+    if stream is not None:
+        st = ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+    _check(load().usbs_sketch_update_static(int(n), int(r), _dev(V_dev), _dev(S_dev),
+                                            _dev(Psi_dev), _dev(P_dev), float(eta), st), None)
