@@ -60,7 +60,7 @@ typedef struct usbs_params {
   int    k_p;              /* past-information columns; only 0 is supported */
   int    r;                /* sketch rank (Sec. 4); 0 = no sketch */
   int    precision;        /* USBS_PRECISION_*; default MIXED */
-  int    lanczos_basis;    /* block Lanczos basis columns J (multiple of 16, <= 64) */
+  int    lanczos_basis;    /* block Lanczos basis columns J: 16, 32 or 64 (at most n - 16) */
   int    lanczos_restarts; /* Rayleigh-Ritz cycles per eigen solve (App. E: 10) */
   double lanczos_tol;      /* stop when the top-k_c Ritz residuals <= tol * |theta|_max */
   double ipm_mu_tol;       /* IPM stops once mu < ipm_mu_tol (App. B.1: 1e-7) */
@@ -79,6 +79,7 @@ typedef struct usbs_eig_info {
   int    matvecs;          /* single-vector products with C - A*(y) (block size x SpMMs) */
   int    converged;        /* 1 if every top-k_c residual met lanczos_tol */
   double max_residual;     /* max over top k_c of ||M v - theta v|| (scaled units) */
+  int    jacobi_sweeps;    /* Jacobi sweeps of the Rayleigh-Ritz steps, summed */
 } usbs_eig_info;
 
 typedef struct usbs_step_info {
@@ -123,7 +124,7 @@ const char* usbs_last_error(const usbs_ctx* ctx);
  * usbs_create -- copy one problem (C, A, b, I) of Sec. 2.1 to the device and set the
  * state to the cold start y_0 = 0, Xbar_0 = 0 (the first solve computes V_0).
  *
- *  n        : order of C and X (n >= 24).
+ *  n        : order of C and X (n >= 32).
  *  C_rowptr : n+1 int64, C_col : nnz int32, C_val : nnz FP64.  C as CSR with BOTH
  *             triangles; diagonal entries allowed; duplicates are summed.
  *  m        : number of constraints; nnzA entries (A_con[e], A_i[e], A_j[e], A_val[e])
@@ -132,7 +133,7 @@ const char* usbs_last_error(const usbs_ctx* ctx);
  *  b        : m FP64.  is_ineq : m uint8, nonzero = row is <A_c, X> <= b_c.
  *  Psi      : n x r FP32 row-major sketch test matrix (Sec. 4), required iff p->r > 0.
  *  p        : parameters (NULL = defaults).
- * Errors: USBS_EINVAL (sizes, index ranges, r > 0 without Psi, n < 24, k_p != 0,
+ * Errors: USBS_EINVAL (sizes, index ranges, r > 0 without Psi, n < 32, k_p != 0,
  * unknown trace), USBS_ENOMEM, USBS_ECUDA.  *out is NULL on failure.
  */
 int usbs_create(usbs_ctx** out, int64_t n, const int64_t* C_rowptr, const int32_t* C_col,

@@ -481,9 +481,19 @@ __global__ void __launch_bounds__(256) k_xupdate(int m, const int* __restrict__ 
   __shared__ double ssv[KSV];
   __shared__ double sred[8 * 39];
   __shared__ double smax[8];
-  if (threadIdx.x == 0) svec8(sc->S, ssv);
+  __shared__ int finite_ok;
+  if (threadIdx.x == 0) {
+    svec8(sc->S, ssv);
+    int ok = isfinite(sc->eta);
+    for (int u = 0; u < KSV; ++u) ok &= isfinite(ssv[u]);
+    finite_ok = ok;
+  }
   __syncthreads();
-  const double eta = sc->eta;
+  // a non-finite subproblem solution must not reach the eigen solve: stay at y and let
+  // the host report USBS_ENUMERIC from the status word
+  const bool okS = finite_ok != 0;
+  if (!okS && blockIdx.x == 0 && threadIdx.x == 0) const_cast<DevScalars*>(sc)->status = USBS_ENUMERIC;
+  const double eta = okS ? sc->eta : 1.0;
   double acc[39];
   double mx = 0.0;
 #pragma unroll
@@ -494,9 +504,9 @@ __global__ void __launch_bounds__(256) k_xupdate(int m, const int* __restrict__ 
     double z = 0.0;
 #pragma unroll
     for (int u = 0; u < KSV; ++u) z += (double)g[u] * ssv[u];
-    const double axc = eta * ax[c] + z;
+    const double axc = okS ? eta * ax[c] + z : ax[c];
     const double bc = b[c];
-    double yc = y[c] - (bc - axc) * inv_rho;
+    double yc = okS ? y[c] - (bc - axc) * inv_rho : y[c];
     const bool iq = ineq[c] != 0;
     if (iq && yc < 0.0) yc = 0.0;
     axnew[c] = axc;
@@ -658,13 +668,35 @@ __global__ void __launch_bounds__(256) k_sketch_update(int n, int r, const T* __
   }
 }
 
-__global__ void k_reduce(const double* __restrict__ partials, int nparts, int nvals,
-                         double* __restrict__ out) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nvals) return;
+// Sum of per-CTA partials, fixed order: a block owns 32 outputs; warp w adds partials
+// w, w + 8, ... (coalesced 256-byte rows), then the 8 warp sums are added in order.
+__global__ void __launch_bounds__(256) k_reduce(const double* __restrict__ partials, int nparts,
+                                                int nvals, double* __restrict__ out,
+                                                const int* __restrict__ mask) {
+  if (mask && *mask == 0) return;
+  __shared__ double ws[8][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x * 32 + lane;
   double s = 0.0;
-  for (int p = 0; p < nparts; ++p) s += partials[(size_t)p * PART_STRIDE + t];
-  out[t] = s;
+  if (t < nvals) {
+    int p = warp;
+    for (; p + 24 < nparts; p += 32) {
+      const double a0 = partials[(size_t)p * PART_STRIDE + t];
+      const double a1 = partials[(size_t)(p + 8) * PART_STRIDE + t];
+      const double a2 = partials[(size_t)(p + 16) * PART_STRIDE + t];
+      const double a3 = partials[(size_t)(p + 24) * PART_STRIDE + t];
+      s += a0; s += a1; s += a2; s += a3;
+    }
+    for (; p < nparts; p += 8) s += partials[(size_t)p * PART_STRIDE + t];
+  }
+  ws[warp][lane] = s;
+  __syncthreads();
+  if (warp == 0 && t < nvals) {
+    double tot = 0.0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) tot += ws[w][lane];
+    out[t] = tot;
+  }
 }
 
 // max-reduce one slot (used for the infinity norm)
@@ -686,9 +718,9 @@ int red_grid(Ctx* c, int64_t rows, int rows_per_cta) {
   return (int)g;
 }
 
-void reduce_partials(Ctx* c, int nparts, int nvals, double* out) {
-  USBS_LAUNCH_B(c, USBS_KIND_REDUCE, 8.0 * nvals * (nparts + 1));
-  k_reduce<<<(nvals + 255) / 256, 256, 0, c->stream>>>(c->partials, nparts, nvals, out);
+void reduce_partials(Ctx* c, int nparts, int nvals, double* out, const int* mask) {
+  USBS_LAUNCH_B(c, USBS_KIND_REDUCE, mask ? 0.0 : 8.0 * nvals * (nparts + 1));
+  k_reduce<<<(nvals + 31) / 32, 256, 0, c->stream>>>(c->partials, nparts, nvals, out, mask);
 }
 
 // CTAs for kernels whose CTA covers 32 rows per iteration (8 warps x 4 rows)

@@ -55,11 +55,15 @@ struct DevLanczos {
   double Rlast[64];            // R of the residual block of the cycle
   double res[KB];              // residual norms of the top k_c Ritz pairs
   double normest;              // running estimate of |M|
-  int dcol[8];                 // columns of the current block replaced by random vectors
-  int defl;                    // a column of the current block was replaced
+  int dcol[8];                 // per column of the current block: 1 = replace by a random
+                               // vector, 2 = zero it (still dependent after two passes)
+  int defl;                    // mask of the second pass: the first pass replaced a column
+  int defl2;                   // mask of the third pass: the second pass replaced a column
   int converged;
   int cycles;
   int status;                  // USBS_ENUMERIC if the projected matrix went non-finite
+  int sweeps;                  // Jacobi sweeps summed over the cycles of this solve
+  int pad2;
 };
 
 template <typename T>
@@ -84,6 +88,7 @@ struct Ctx {
   int num_sms = 152;
   std::string err;
   bool started = false;         // an iterate exists (cold start done)
+  bool debug = false;           // USBS_DEBUG=1: per-block-step checks on the host
   long long total_matvecs = 0;
 
   // operator (scaled): merged off-diagonal CSR pattern + diagonal
@@ -228,8 +233,19 @@ template <typename T> struct Bulk {
   static void gram_xy(Ctx* c, const void* X, const void* Y, int nparts);
 };
 
+// shared-memory-staged block Gram-Schmidt kernels (orth.cu); grid = orth_grid(c, n)
+template <typename T> struct Orth {
+  static void proj(Ctx* c, const void* Qb, int nb, const void* W, const int* mask);
+  static void update(Ctx* c, const void* Qb, int nb, void* W, const int* mask);
+  static void finalize(Ctx* c, const void* Qb, int nb, const void* W, void* out, const int* mask,
+                       uint64_t seed);
+  static void restart(Ctx* c, const void* Qb, int J, int nout, const double* Y, void* out,
+                      const void* resid, int resid_slot);
+};
+int orth_grid(Ctx* c, int64_t rows);
+
 int red_grid(Ctx* c, int64_t rows, int rows_per_cta);
-void reduce_partials(Ctx* c, int nparts, int nvals, double* out);
+void reduce_partials(Ctx* c, int nparts, int nvals, double* out, const int* mask = nullptr);
 
 void reduce_max_slot(Ctx* c, int nparts, int slot, double* out);
 

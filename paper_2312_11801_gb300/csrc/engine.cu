@@ -3,6 +3,7 @@
 // extern "C" entry points declared in include/usbs.h.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <utility>
@@ -114,7 +115,7 @@ static int preprocess(Ctx* c, int64_t n, const int64_t* C_rowptr, const int32_t*
                       const double* C_val, int64_t m, int64_t nnzA, const int32_t* A_con,
                       const int32_t* A_i, const int32_t* A_j, const double* A_val,
                       const double* b, const uint8_t* is_ineq, double trace_hint, HostProblem& hp) {
-  if (n < 24 || n > 0x7fffffff - 1) { c->err = "n must be in [24, 2^31-1)"; return USBS_EINVAL; }
+  if (n < 32 || n > 0x7fffffff - 1) { c->err = "n must be in [32, 2^31-1)"; return USBS_EINVAL; }
   if (m < 1 || m > 0x7fffffff - 1) { c->err = "m must be in [1, 2^31-1)"; return USBS_EINVAL; }
   if (nnzA < 1 || nnzA > 0x7fffffff - 1) { c->err = "nnzA must be in [1, 2^31-1)"; return USBS_EINVAL; }
   if (!C_rowptr || !b || !A_con || !A_i || !A_j || !A_val || !is_ineq) {
@@ -436,9 +437,12 @@ static int init_ctx(Ctx* c, int64_t n, int64_t m, int64_t nnzA, const usbs_param
   int J = q.lanczos_basis > 0 ? q.lanczos_basis : 64;
   J = std::min(J, JMAX);
   J = (J / 16) * 16;
-  const int cap = (int)std::min<int64_t>(JMAX, 16 * ((n - 8) / 16));
+  // the basis plus the residual block must leave at least one block of room in R^n,
+  // so that random replacement columns always have an orthogonal complement to live in
+  const int cap = (int)std::min<int64_t>(JMAX, 16 * ((n - 16) / 16));
   J = std::min(J, cap);
-  if (J < 16) { c->err = "Lanczos basis < 16 (n too small)"; return USBS_EINVAL; }
+  if (J == 48) J = 32;   // the Ritz kernel is specialised for J in {16, 32, 64}
+  if (J < 16) { c->err = "n too small: need n >= 32 (Lanczos basis of 16 plus two blocks)"; return USBS_EINVAL; }
   c->J = J;
   c->keep = J / 2;
   c->seed = q.seed;
@@ -451,6 +455,8 @@ static int init_cuda(Ctx* c) {
   if (q.device >= 0) USBS_CUDA_TRY(c, cudaSetDevice(q.device));
   USBS_CUDA_TRY(c, cudaGetDevice(&c->device));
   USBS_CUDA_TRY(c, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+  const char* dbg = std::getenv("USBS_DEBUG");
+  c->debug = dbg && dbg[0] == '1';
   if (q.stream) {
     c->stream = (cudaStream_t)q.stream;
     c->own_stream = false;
@@ -466,25 +472,55 @@ static int init_cuda(Ctx* c) {
 // ---------------------------------------------------------------------------------------
 template <typename T>
 static void orth_block(Ctx* c, T* Q, int nb, T* W, T* out, int j, int write_T, int is_resid) {
-  const int np = red_grid(c, c->n, 64);
+  const int np = orth_grid(c, c->n);
   const int* defl = DEV_FIELD(c->lz, DevLanczos, defl, int);
   if (nb > 0) {
-    Bulk<T>::proj(c, Q, nb, W, np, nullptr);
+    Orth<T>::proj(c, Q, nb, W, nullptr);
     reduce_partials(c, np, nb * 64, c->red + RED_H);
   }
-  Bulk<T>::update_proj(c, Q, nb, W, np, nullptr);
+  Orth<T>::update(c, Q, nb, W, nullptr);
   reduce_partials(c, np, 576, c->red + RED_H2);
   launch_chol_block(c, j, nb, write_T, is_resid, 0);
-  Bulk<T>::finalize(c, Q, nb, W, out, np, nullptr, c->seed + 0x1000003ull * (c->rng_counter++));
-  // masked second pass: only runs when a column was replaced by a random vector
-  if (nb > 0) {
-    Bulk<T>::proj(c, Q, nb, out, np, defl);
-    reduce_partials(c, np, nb * 64, c->red + RED_H);
+  Orth<T>::finalize(c, Q, nb, W, out, nullptr, c->seed + 0x1000003ull * (c->rng_counter++));
+  // masked second and third passes: only run when a column was replaced by a random
+  // vector (the third zeroes what is still dependent after it)
+  const int* defl2 = DEV_FIELD(c->lz, DevLanczos, defl2, int);
+  for (int pass = 1; pass <= 2; ++pass) {
+    const int* mask = pass == 1 ? defl : defl2;
+    if (nb > 0) {
+      Orth<T>::proj(c, Q, nb, out, mask);
+      reduce_partials(c, np, nb * 64, c->red + RED_H, mask);
+    }
+    Orth<T>::update(c, Q, nb, out, mask);
+    reduce_partials(c, np, 576, c->red + RED_H2, mask);
+    launch_chol_block(c, j, nb, 0, is_resid, pass);
+    Orth<T>::finalize(c, Q, nb, out, out, mask, c->seed + 0x2000011ull * (c->rng_counter++));
   }
-  Bulk<T>::update_proj(c, Q, nb, out, np, defl);
-  reduce_partials(c, np, 576, c->red + RED_H2);
-  launch_chol_block(c, j, nb, 0, 0, 1);
-  Bulk<T>::finalize(c, Q, nb, out, out, np, defl, 0);
+}
+
+// USBS_DEBUG=1: after every block step, synchronise and check the projected matrix,
+// the reduced projections and the new block's R factor; print the first non-finite one.
+static void debug_block(Ctx* c, int cycle, int j) {
+  cudaStreamSynchronize(c->stream);
+  std::vector<double> red(RED_TOTAL);
+  cudaMemcpy(red.data(), c->red, sizeof(double) * RED_TOTAL, cudaMemcpyDeviceToHost);
+  cudaMemcpy(c->h_lz, c->lz, sizeof(DevLanczos), cudaMemcpyDeviceToHost);
+  auto bad = [](const double* p, int k) {
+    for (int i = 0; i < k; ++i)
+      if (!std::isfinite(p[i])) return i;
+    return -1;
+  };
+  int bT = bad(c->h_lz->T, JMAX * JMAX), bH = bad(red.data() + RED_H, 512),
+      bH2 = bad(red.data() + RED_H2, 576), bR = bad(c->h_lz->Rinv, 64);
+  double gmin = 1e300, gmax = 0.0;
+  for (int a = 0; a < 8; ++a) {
+    gmin = std::min(gmin, red[RED_GRAM + a * 9]);
+    gmax = std::max(gmax, red[RED_GRAM + a * 9]);
+  }
+  std::fprintf(stderr, "usbs debug: cycle %d block %d defl %d dcol %d%d%d%d%d%d%d%d gram diag [%.3e, %.3e] "
+               "badT %d badH %d badH2 %d badRinv %d\n", cycle, j, c->h_lz->defl, c->h_lz->dcol[0],
+               c->h_lz->dcol[1], c->h_lz->dcol[2], c->h_lz->dcol[3], c->h_lz->dcol[4], c->h_lz->dcol[5],
+               c->h_lz->dcol[6], c->h_lz->dcol[7], gmin, gmax, bT, bH, bH2, bR);
 }
 
 struct LanczosOut {
@@ -517,6 +553,7 @@ static int lanczos(Ctx* c, const double* y_dev, const void* start, void* out_vec
       Bulk<T>::spmm(c, valM, c->dM, Q + j * bs, W);
       matvecs += 8;
       orth_block<T>(c, Q, j + 1, W, Q + (j + 1) * bs, j, 1, j == nblk - 1);
+      if (c->debug) debug_block(c, cycle, j);
     }
     launch_ritz(c, J, keep);
     USBS_TRY(check_launch(c, "lanczos cycle"));
@@ -528,14 +565,14 @@ static int lanczos(Ctx* c, const double* y_dev, const void* start, void* out_vec
       return USBS_ENUMERIC;
     }
     if (c->h_lz->converged || cycle == c->prm.lanczos_restarts - 1) break;
-    Bulk<T>::restart_gemm(c, Q, J, keep / 8, DEV_FIELD(c->lz, DevLanczos, Y, double), Q2,
-                          Q + nblk * bs, keep / 8);
+    Orth<T>::restart(c, Q, J, keep / 8, DEV_FIELD(c->lz, DevLanczos, Y, double), Q2,
+                     Q + nblk * bs, keep / 8);
     std::swap(Q, Q2);
     nb0 = keep / 8;
   }
   c->Q = Q;
   c->Q2 = Q2;
-  Bulk<T>::restart_gemm(c, Q, J, 1, DEV_FIELD(c->lz, DevLanczos, Y, double), out_vecs, nullptr, 0);
+  Orth<T>::restart(c, Q, J, 1, DEV_FIELD(c->lz, DevLanczos, Y, double), out_vecs, nullptr, 0);
   USBS_TRY(check_launch(c, "lanczos output"));
   if (lo) {
     lo->cycles = c->h_lz->cycles;
@@ -645,7 +682,7 @@ static int step_impl(Ctx* c, usbs_step_info* info) {
   fill_info(c, *c->h_sc, lo.matvecs, info);
   if (info) info->n_alt = n_alt;
   if (c->h_sc->status != 0) {
-    c->err = "non-finite value in the FP64 step";
+    c->err = "non-finite value in the subproblem, the model value or the gates";
     return USBS_ENUMERIC;
   }
   return USBS_OK;
@@ -755,6 +792,7 @@ int usbs_extreme_eigs(usbs_ctx* ctx, const double* y, int kc, double* evals, dou
     info->matvecs = lo.matvecs;
     info->converged = lo.converged;
     info->max_residual = lo.max_res;
+    info->jacobi_sweeps = c->h_lz->sweeps;
   }
   return USBS_OK;
 }

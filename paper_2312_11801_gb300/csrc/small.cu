@@ -253,9 +253,13 @@ __device__ double warp_lambda_max(const double* A, int k, float* Af, float* Vf) 
 // orthogonal to Q).  A column whose squared norm after orthogonalisation falls below
 // rel_thr times its squared norm before it is deficient: it is replaced by a random
 // vector (k_finalize) and the block is orthogonalised once more (the masked pass).
+// pass 0: the new block (writes T, R_last, and the second pass's mask); pass 1: masked by
+// defl, replaces still-dependent columns again and sets the third pass's mask; pass 2:
+// masked by defl2, zeroes what is still dependent.
 __global__ void k_chol_block(DevLanczos* lz, const double* __restrict__ red, int j, int nb,
                              int write_T, int is_resid, int defl_pass, double rel_thr) {
-  if (defl_pass && lz->defl == 0) return;
+  if (defl_pass == 1 && lz->defl == 0) return;
+  if (defl_pass == 2 && lz->defl2 == 0) return;
   __shared__ double G[64], pre[8], R[64], Ri[64];
   __shared__ int dc[8];
   const double* H = red + RED_H;
@@ -284,6 +288,7 @@ __global__ void k_chol_block(DevLanczos* lz, const double* __restrict__ red, int
     G[tid] = g;
   }
   __syncthreads();
+  __shared__ double premax;
   if (tid < 8) {
     double p = G[tid * 8 + tid];
     for (int b = 0; b < nb; ++b)
@@ -292,6 +297,12 @@ __global__ void k_chol_block(DevLanczos* lz, const double* __restrict__ red, int
         p += h * h;
       }
     pre[tid] = p;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double m = 0.0;
+    for (int a = 0; a < 8; ++a) m = fmax(m, pre[a]);
+    premax = m;
   }
   __syncthreads();
   if (tid < 32) {
@@ -311,7 +322,9 @@ __global__ void k_chol_block(DevLanczos* lz, const double* __restrict__ red, int
           if (l < j) d -= rc[l] * rc[l];
       }
       d = __shfl_sync(FULL, d, j);
-      const bool bad = !(d > rel_thr * pre[j]) || !(pre[j] > 0.0);
+      // deficient: small against the column's own norm before orthogonalisation, or
+      // against the block's largest column (a residual at rounding level)
+      const bool bad = !(d > rel_thr * pre[j]) || !(d > rel_thr * rel_thr * premax) || !(pre[j] > 0.0);
       if (bad) {
         badmask |= 1 << j;
         if (lane == j) rc[j] = 1.0;   // row j of R stays e_j^T: the column is replaced
@@ -348,21 +361,30 @@ __global__ void k_chol_block(DevLanczos* lz, const double* __restrict__ red, int
       }
 #pragma unroll
       for (int i = 0; i < 8; ++i) Ri[i * 8 + cidx] = x[i];
-      dc[lane] = ((badmask >> lane) & 1) && !defl_pass;
+      const int isbad = (badmask >> lane) & 1;
+      dc[lane] = isbad ? (defl_pass < 2 ? 1 : 2) : 0;
     }
     __syncwarp();
     for (int u = lane; u < 64; u += 32) {
       lz->R[u] = R[u];
       lz->Rinv[u] = Ri[u];
-      if (is_resid && !defl_pass) {
-        const int i = u / 8, jj = u % 8;
+      const int i = u / 8, jj = u % 8;
+      if (is_resid && defl_pass == 0)
         lz->Rlast[u] = (i == jj && dc[i]) ? 0.0 : R[u];   // deficient rows carry no residual
-      }
+      else if (is_resid && defl_pass == 2 && dc[i])
+        lz->Rlast[u] = 0.0;                              // zeroed columns carry none either
     }
     if (lane < 8) lz->dcol[lane] = dc[lane];
-    // the masked second pass reads this flag in every one of its kernels, so only the
-    // first pass of the next block may change it
-    if (lane == 0 && !defl_pass) lz->defl = (badmask != 0) ? 1 : 0;
+    // each masked pass reads its flag in every one of its kernels, so a flag is only
+    // changed by the pass before it
+    if (lane == 0) {
+      if (defl_pass == 0) {
+        lz->defl = (badmask != 0) ? 1 : 0;
+        lz->defl2 = 0;
+      } else if (defl_pass == 1) {
+        lz->defl2 = (badmask != 0) ? 1 : 0;
+      }
+    }
   }
 }
 
@@ -374,16 +396,18 @@ __global__ void k_chol_block(DevLanczos* lz, const double* __restrict__ red, int
 // sort, the kept Ritz vectors are orthonormalised (classical Gram-Schmidt, two passes)
 // and the restarted projected matrix is Y_keep^T T Y_keep, so rounding in the
 // rotations does not leak into the next cycle.
-template <typename S>
-__global__ void __launch_bounds__(512) k_ritz(DevLanczos* lz, int J, int keep, int kc, double tol,
-                                              int max_sweeps, double jac_eps) {
+template <typename S, int J>
+__global__ void __launch_bounds__(512) k_ritz(DevLanczos* lz, int kc, double tol, int max_sweeps,
+                                              double jac_eps) {
+  constexpr int keep = J / 2;
+  constexpr int half = J / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int LD = JMAX + 1;
+  constexpr int LD = J + 1;
   S* A = reinterpret_cast<S*>(smem_raw);      // J x LD: T, rotated in place
-  S* Vv = A + JMAX * LD;                        // J x LD: accumulated rotations
-  S* Tc = Vv + JMAX * LD;                       // J x LD: copy of T
-  S* Y = Tc + JMAX * LD;                        // J x LD: sorted Ritz vectors
-  S* Z = Y + JMAX * LD;                         // J x keep: T Y_keep
+  S* Vv = A + J * LD;                           // J x LD: accumulated rotations
+  S* Tc = Vv + J * LD;                          // J x LD: copy of T
+  S* Y = Tc + J * LD;                           // J x LD: sorted Ritz vectors
+  S* Z = Y + J * LD;                            // J x keep: T Y_keep
   __shared__ S cs[JMAX / 2], sn[JMAX / 2];
   __shared__ int pp[JMAX / 2], qq[JMAX / 2];
   __shared__ double th[JMAX];
@@ -416,7 +440,7 @@ __global__ void __launch_bounds__(512) k_ritz(DevLanczos* lz, int J, int keep, i
     if (tid < JMAX) lz->theta[tid] = 0.0;
     return;
   }
-  const int half = J / 2;
+  const S skip = (S)(jac_eps * 1e-2), big = (S)1e18;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     double off = 0.0, tot = 0.0;
     for (int t = tid; t < J * J; t += blockDim.x) {
@@ -438,6 +462,7 @@ __global__ void __launch_bounds__(512) k_ritz(DevLanczos* lz, int J, int keep, i
     }
     __syncthreads();
     if (stop) break;
+    if (tid == 0) lz->sweeps += 1;
     for (int round = 0; round < J - 1; ++round) {
       if (tid < half) {
         // circle method: position 0 fixed, the others rotate
@@ -451,11 +476,11 @@ __global__ void __launch_bounds__(512) k_ritz(DevLanczos* lz, int J, int keep, i
         const S apq = A[p * LD + q];
         S c = (S)1, sv = (S)0;
         const S app = A[p * LD + p], aqq = A[q * LD + q];
-        if (fabs((double)apq) > 1e-300 &&
-            fabs((double)apq) > (double)jac_eps * 1e-2 * sqrt(fabs((double)app * (double)aqq))) {
+        // all in S: an FP64 sqrt here would be a long FP64 sequence every round
+        if (apq != (S)0 && fabs(apq) > skip * sqrt(fabs(app * aqq))) {
           const S tau = (aqq - app) / ((S)2 * apq);
           S t;
-          if (fabs((double)tau) > 1e18) t = (S)0.5 / tau;
+          if (fabs(tau) > big) t = (S)0.5 / tau;
           else t = (tau >= (S)0 ? (S)1 : (S)-1) / (fabs(tau) + sqrt(tau * tau + (S)1));
           c = (S)1 / sqrt(t * t + (S)1);
           sv = t * c;
@@ -464,9 +489,10 @@ __global__ void __launch_bounds__(512) k_ritz(DevLanczos* lz, int J, int keep, i
         sn[k] = sv;
       }
       __syncthreads();
-      // A <- G^T A G on 2 x 2 blocks; V <- V G
-      for (int t = tid; t < half * half + J * half; t += blockDim.x) {
-        if (t < half * half) {
+      // A <- G^T A G on 2 x 2 blocks; V <- V G (index arithmetic on powers of two)
+      constexpr int NBLK = half * half, NITEM = half * half + J * half;
+      for (int t = tid; t < NITEM; t += blockDim.x) {
+        if (t < NBLK) {
           const int k1 = t / half, k2 = t % half;
           const int p1 = pp[k1], q1 = qq[k1], p2 = pp[k2], q2 = qq[k2];
           const S c1 = cs[k1], s1 = sn[k1], c2 = cs[k2], s2 = sn[k2];
@@ -481,7 +507,7 @@ __global__ void __launch_bounds__(512) k_ritz(DevLanczos* lz, int J, int keep, i
           A[q1 * LD + p2] = c2 * rc - s2 * rd;
           A[q1 * LD + q2] = s2 * rc + c2 * rd;
         } else {
-          const int u = t - half * half;
+          const int u = t - NBLK;
           const int k = u / J, row = u % J;
           const S c = cs[k], sv = sn[k];
           const int p = pp[k], q = qq[k];
@@ -569,17 +595,22 @@ __global__ void __launch_bounds__(512) k_ritz(DevLanczos* lz, int J, int keep, i
   // Ritz values of the orthonormalised vectors (Rayleigh quotients) and residual norms
   // ||R_last E^T y_i|| for the top k_c
   if (tid < kc) {
+    // residual of the Ritz pair (theta_i, Q y_i): Q (T y_i - theta_i y_i) + Q_res R E^T y_i,
+    // two orthogonal terms (y_i is only an approximate eigenvector of T)
     const int i = tid;
     S zz = (S)0;
     for (int r = 0; r < J; ++r) zz += Y[r * LD + i] * Z[r * keep + i];
     th[i] = (double)zz;
     double s2 = 0.0;
+    for (int r = 0; r < J; ++r) {
+      const double e = (double)Z[r * keep + i] - (double)zz * (double)Y[r * LD + i];
+      s2 += e * e;
+    }
     for (int a = 0; a < 8; ++a) {
       double v = 0.0;
       for (int c2 = a; c2 < 8; ++c2) v += lz->Rlast[a * 8 + c2] * (double)Y[(J - 8 + c2) * LD + i];
       s2 += v * v;
     }
-    hbuf[i] = (S)0;
     lz->res[i] = sqrt(s2);
   }
   __syncthreads();
@@ -764,6 +795,8 @@ __global__ void __launch_bounds__(256) k_ipm(DevScalars* sc, const double* __res
     __syncthreads();
     // Gaussian elimination with partial pivoting
     const int LDL = K + 1;
+    if (tid == 0) sh.piv = 0;
+    __syncthreads();
     for (int p = 0; p < K; ++p) {
       if (warp == 0) {
         double best = -1.0;
@@ -784,7 +817,13 @@ __global__ void __launch_bounds__(256) k_ipm(DevScalars* sc, const double* __res
             sh.L[bi * LDL + c] = x;
           }
         __syncwarp();
-        if (lane == 0) sh.fcol[p] = 1.0 / sh.L[p * LDL + p];
+        if (lane == 0) {
+          // an exactly singular system (possible at degenerate optima): mark the
+          // direction unusable instead of dividing by zero
+          const double pv = sh.L[p * LDL + p];
+          sh.fcol[p] = (fabs(pv) > 1e-300) ? 1.0 / pv : 0.0;
+          if (!(fabs(pv) > 1e-300)) sh.piv = -1;
+        }
       }
       __syncthreads();
       const double ipv = sh.fcol[p];
@@ -832,6 +871,15 @@ __global__ void __launch_bounds__(256) k_ipm(DevScalars* sc, const double* __res
       sh.dt[r] = x;
     }
     __syncthreads();
+    // a non-finite Newton direction (singular system): keep the current strictly
+    // feasible iterate and stop
+    if (tid == 0) {
+      bool fin = isfinite(sh.deta) && isfinite(sh.domega) && isfinite(sh.dzeta) && sh.piv >= 0;
+      for (int c = 0; c < K && fin; ++c) fin = isfinite(sh.ds[c]) && isfinite(sh.dt[c]);
+      sh.done = fin ? 0 : 2;
+    }
+    __syncthreads();
+    if (sh.done == 2) break;
     if (tid < 64) {
       // smat of ds, dt
       const int p = tid / 8, q = tid % 8;
@@ -1015,6 +1063,7 @@ __global__ void k_commit(int m, const DevScalars* __restrict__ sc, const double*
 __global__ void k_lanczos_reset(DevLanczos* lz) {
   for (int t = threadIdx.x; t < JMAX * JMAX; t += blockDim.x) lz->T[t] = 0.0;
   if (threadIdx.x == 0) {
+    lz->sweeps = 0;
     lz->status = 0;
     lz->defl = 0;
     lz->converged = 0;
@@ -1027,36 +1076,53 @@ __global__ void k_lanczos_reset(DevLanczos* lz) {
 
 static bool g_attr_done = false;
 
-// dynamic shared memory of k_ritz: A, V, T, Y (J x (J+1)) and T Y_keep (J x J), type S
-static size_t ritz_smem(size_t es) { return es * (4 * JMAX * (JMAX + 1) + JMAX * JMAX); }
+// dynamic shared memory of k_ritz: A, V, T, Y (J x (J+1)) and T Y_keep (J x J/2), type S
+static size_t ritz_smem(size_t es, int J) { return es * (4 * J * (J + 1) + J * J / 2); }
+
+template <typename S, int J>
+static void ritz_attr() {
+  cudaFuncSetAttribute(k_ritz<S, J>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)ritz_smem(sizeof(S), J));
+}
 
 void small_init_attributes() {
   if (g_attr_done) return;
-  const size_t sd = ritz_smem(sizeof(double));
-  const size_t sf = ritz_smem(sizeof(float));
-  cudaFuncSetAttribute(k_ritz<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sd);
-  cudaFuncSetAttribute(k_ritz<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf);
+  ritz_attr<double, 16>(); ritz_attr<double, 32>(); ritz_attr<double, 64>();
+  ritz_attr<float, 16>(); ritz_attr<float, 32>(); ritz_attr<float, 64>();
   g_attr_done = true;
 }
 
 void launch_chol_block(Ctx* c, int j, int nb, int write_T, int is_resid, int defl_pass) {
   USBS_LAUNCH(c, USBS_KIND_SMALL);
-  const double thr = c->fp64 ? 1e-20 : 1e-9;
+  // a column keeps about eps / (norm after / norm before) of orthogonality to the basis:
+  // replace it when that ratio drops below 1e-3 (FP32) or 1e-8 (FP64)
+  const double thr = c->fp64 ? 1e-16 : 1e-6;
   k_chol_block<<<1, 64, 0, c->stream>>>(c->lz, c->red, j, nb, write_T, is_resid, defl_pass, thr);
+}
+
+template <typename S>
+static void launch_ritz_t(Ctx* c, int J, int max_sweeps, double eps) {
+  const size_t sm = ritz_smem(sizeof(S), J);
+  const int threads = J >= 64 ? 512 : 256;
+  if (J == 16)
+    k_ritz<S, 16><<<1, threads, sm, c->stream>>>(c->lz, c->kc, c->prm.lanczos_tol, max_sweeps, eps);
+  else if (J == 32)
+    k_ritz<S, 32><<<1, threads, sm, c->stream>>>(c->lz, c->kc, c->prm.lanczos_tol, max_sweeps, eps);
+  else
+    k_ritz<S, 64><<<1, threads, sm, c->stream>>>(c->lz, c->kc, c->prm.lanczos_tol, max_sweeps, eps);
 }
 
 void launch_ritz(Ctx* c, int J, int keep) {
   USBS_LAUNCH(c, USBS_KIND_SMALL);
+  (void)keep;   // keep = J / 2, fixed by the specialisation
   small_init_attributes();
   if (c->fp64) {
-    const size_t sm = ritz_smem(sizeof(double));
-    k_ritz<double><<<1, 512, sm, c->stream>>>(c->lz, J, keep, c->kc, c->prm.lanczos_tol, 30, 1e-14);
+    launch_ritz_t<double>(c, J, 30, 1e-14);
   } else {
-    const size_t sm = ritz_smem(sizeof(float));
     // FP32 rotations reach an off-diagonal floor near J * 2^-24 of ||T||: stop at 1e-5.
     // The restart uses the exact projection Y_keep^T T Y_keep, so loose rotations only
     // cost convergence speed, not accuracy.
-    k_ritz<float><<<1, 512, sm, c->stream>>>(c->lz, J, keep, c->kc, c->prm.lanczos_tol, 12, 1e-5);
+    launch_ritz_t<float>(c, J, 12, 1e-5);
   }
 }
 

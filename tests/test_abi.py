@@ -61,8 +61,8 @@ def test_invalid_arguments_rejected_on_the_host(U):
     _expect_einval(U, p, "k_p", k_p=1)
     _expect_einval(U, p, "k_c", k_c=9)
     _expect_einval(U, p, "Psi", r=4)
-    small = I.maxcut_er(20, 4, seed=1)
-    _expect_einval(U, small, "n too small")
+    small = I.maxcut_er(28, 4, seed=1)
+    _expect_einval(U, small, "n >= 32")
     bad = I.maxcut_er(40, 4, seed=1)
     bad.A_i = bad.A_i.copy(); bad.A_i[3] = 40
     _expect_einval(U, bad, "A index out of range")

@@ -75,7 +75,7 @@ def test_solve_matches_oracle(mods, name, precision):
 
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("name,value", [
-    ("K24", 24 * 24 / 4), ("C25", 12.5 * (1 + math.cos(math.pi / 25))), ("torus8", 128.0)])
+    ("K32", 32 * 32 / 4), ("C33", 16.5 * (1 + math.cos(math.pi / 33))), ("torus8", 128.0)])
 def test_closed_form_maxcut(mods, name, value, precision):
     torch, U = mods
     if name == "torus8":
