@@ -284,6 +284,74 @@ long long usbs_launch_count(const usbs_ctx* ctx);
 int usbs_sketch_update_static(int64_t n, int r, const float* V_dev, const double* S_dev,
                               const float* Psi_dev, float* P_dev, double eta, void* stream);
 
+/* ---------------------------------------------------------------------------------
+ * Serving and batching.  The paper has no counterpart for these: they are the service
+ * forms built around its solver.  Requests enter a FIFO queue; one is admitted when a
+ * solve slot is free and its device footprint fits the memory budget.  Each slot is a
+ * host thread with its own CUDA stream, so admitted solves overlap on the GPU
+ * (continuous batching).  Finished instances stay device-resident in an LRU cache; a
+ * request that names a cached instance as its parent is warm-started from it with
+ * usbs_grow, as the paper warm-starts grown instances (Sec. 5.1).
+ * --------------------------------------------------------------------------------- */
+typedef struct usbs_server usbs_server;
+
+typedef struct usbs_server_params {
+  uint64_t hbm_budget_bytes; /* device bytes for resident instances; 0 = 80% of free memory */
+  int      max_slots;        /* solves running at once (1..256); default 8 */
+  int      cache_entries;    /* finished instances kept for warm starts; default 16 */
+  int      dry_run;          /* 1 = no GPU: a request holds its slot for fake_service_s */
+  usbs_params solver;        /* parameters of every instance (the stream field is ignored) */
+} usbs_server_params;
+
+typedef struct usbs_completion {
+  int64_t  request_id;
+  int64_t  parent_id;        /* -1 = cold start requested */
+  int      status;           /* USBS_OK, USBS_ENOTCONV, USBS_EBUSY (never fits), or an error */
+  int      warm;             /* 1 = warm-started from the resident parent */
+  int      iters;            /* USBS iterations of the solve */
+  int      slot;             /* solve slot that ran it */
+  double   objective, dual_bound, relgap, relinf;
+  double   t_arrival, t_admit, t_finish;   /* seconds since usbs_server_create */
+  uint64_t bytes;            /* device bytes reserved for the instance */
+} usbs_completion;
+
+typedef struct usbs_server_stats {
+  uint64_t used_bytes, peak_bytes, budget_bytes;
+  int      pending, running, peak_running, cached;
+  int64_t  finished, rejected;
+} usbs_server_stats;
+
+/* Device footprint of one context, as usbs_create allocates it (an upper bound). */
+uint64_t usbs_instance_bytes(int64_t n, int64_t nnzC, int64_t m, int64_t nnzA, int r,
+                             int precision);
+
+void usbs_server_params_default(usbs_server_params* p);
+int usbs_server_create(usbs_server** out, const usbs_server_params* p);
+
+/* Queue one solve.  The problem arguments are those of usbs_create (copied).  parent_id
+ * >= 0 asks for a warm start from that finished request if it is still resident (the new
+ * problem must extend the parent's as usbs_grow requires); otherwise the solve is cold.
+ * fake_service_s is used only in dry-run mode. */
+int usbs_server_submit(usbs_server* s, int64_t request_id, int64_t parent_id, int64_t n,
+                       const int64_t* C_rowptr, const int32_t* C_col, const double* C_val,
+                       int64_t m, int64_t nnzA, const int32_t* A_con, const int32_t* A_i,
+                       const int32_t* A_j, const double* A_val, const double* b,
+                       const uint8_t* is_ineq, const float* Psi, double tol,
+                       double fake_service_s);
+
+/* Move up to max finished requests into out (waiting up to wait_ms for the first one).
+ * Returns how many were written, or a negative status. */
+int usbs_server_poll(usbs_server* s, usbs_completion* out, int max, int wait_ms);
+int usbs_server_get_stats(usbs_server* s, usbs_server_stats* st);
+/* Finish every queued and running request, then free the server and its cache. */
+int usbs_server_destroy(usbs_server* s);
+
+/* Solve `count` contexts from their cold start, up to max_concurrency at a time (each on
+ * its own stream and host thread).  results[i] and status[i] (may be NULL) per context;
+ * returns the first hard error, else USBS_OK. */
+int usbs_batch_solve(usbs_ctx** ctxs, int count, double tol, int max_concurrency,
+                     usbs_result* results, int* status);
+
 /* Scaling of the problem: c = ||C||_F and tau = tr(X*) (App. E). */
 int usbs_scaling(const usbs_ctx* ctx, double* c_scale, double* tau);
 

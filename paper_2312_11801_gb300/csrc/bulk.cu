@@ -5,6 +5,8 @@
 // Row kernels use one warp per 4 rows: lane L works on row (L >> 3) and on column
 // a = L & 7 of an n x 8 row-major block, so the 8 lanes of a row read one 32-byte
 // (float) or 64-byte (double) row segment together.
+#include <mutex>
+
 #include "common.cuh"
 
 namespace usbs {
@@ -805,11 +807,10 @@ template <typename T>
 void Bulk<T>::gstats(Ctx* c, const void* V, const double* ax, const double* y, int nparts) {
   USBS_LAUNCH_B(c, USBS_KIND_CONSTR, constr_bytes(c, sizeof(T), 24.0));
   size_t smem = sizeof(T) * GS_ROWS * AUG + sizeof(double) * 4 * 880;
-  static bool attr = false;
-  if (!attr) {
+  static std::once_flag once;
+  std::call_once(once, [&] {
     cudaFuncSetAttribute(k_gstats<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
-  }
+  });
   k_gstats<T><<<nparts, 256, smem, c->stream>>>((int)c->m, c->con_ptr, c->ent_i, c->ent_j,
                                                   (const T*)c->ent_v, (const T*)V, ax, y, c->b,
                                                   1.0 / c->prm.rho, c->partials);

@@ -908,38 +908,41 @@ int usbs_set_state(usbs_ctx* ctx, const double* st) {
   if (!ctx || !st) return USBS_EINVAL;
   Ctx* c = reinterpret_cast<Ctx*>(ctx);
   const int64_t m = c->m, n = c->n;
+  // writes go on the context's stream (a pageable cudaMemcpy may return before its DMA
+  // lands, and the stream is non-blocking), with one synchronisation at the end
   USBS_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   std::vector<double> y(m), ax(m);
   for (int64_t i = 0; i < m; ++i) {
     y[i] = st[i] / c->c_scale;
     ax[i] = st[m + i] / c->tau;
   }
-  USBS_CUDA_TRY(c, cudaMemcpy(c->y, y.data(), sizeof(double) * m, cudaMemcpyHostToDevice));
-  USBS_CUDA_TRY(c, cudaMemcpy(c->ax, ax.data(), sizeof(double) * m, cudaMemcpyHostToDevice));
+  USBS_CUDA_TRY(c, cudaMemcpyAsync(c->y, y.data(), sizeof(double) * m, cudaMemcpyHostToDevice, c->stream));
+  USBS_CUDA_TRY(c, cudaMemcpyAsync(c->ax, ax.data(), sizeof(double) * m, cudaMemcpyHostToDevice, c->stream));
   USBS_CUDA_TRY(c, cudaMemcpy(c->h_sc, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost));
   c->h_sc->cx = st[2 * m] / (c->c_scale * c->tau);
   c->h_sc->tr = st[2 * m + 1] / c->tau;
   c->h_sc->f_y = st[2 * m + 2] / (c->c_scale * c->tau);
   c->h_sc->status = 0;
-  USBS_CUDA_TRY(c, cudaMemcpy(c->sc, c->h_sc, sizeof(DevScalars), cudaMemcpyHostToDevice));
+  USBS_CUDA_TRY(c, cudaMemcpyAsync(c->sc, c->h_sc, sizeof(DevScalars), cudaMemcpyHostToDevice, c->stream));
   const double* Vi = st + 2 * m + 3;
   if (c->fp64) {
     std::vector<double> Vb((size_t)8 * n, 0.0);
     for (int64_t i = 0; i < n; ++i)
       for (int a = 0; a < c->kc; ++a) Vb[i * 8 + a] = Vi[i * c->kc + a];
-    USBS_CUDA_TRY(c, cudaMemcpy(c->V, Vb.data(), Vb.size() * sizeof(double), cudaMemcpyHostToDevice));
+    USBS_CUDA_TRY(c, cudaMemcpyAsync(c->V, Vb.data(), Vb.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   } else {
     std::vector<float> Vb((size_t)8 * n, 0.f);
     for (int64_t i = 0; i < n; ++i)
       for (int a = 0; a < c->kc; ++a) Vb[i * 8 + a] = (float)Vi[i * c->kc + a];
-    USBS_CUDA_TRY(c, cudaMemcpy(c->V, Vb.data(), Vb.size() * sizeof(float), cudaMemcpyHostToDevice));
+    USBS_CUDA_TRY(c, cudaMemcpyAsync(c->V, Vb.data(), Vb.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
   }
   if (c->r) {
     std::vector<float> P((size_t)n * c->r);
     const double* Pi = Vi + n * c->kc;
     for (size_t u = 0; u < P.size(); ++u) P[u] = (float)(Pi[u] / c->tau);
-    USBS_CUDA_TRY(c, cudaMemcpy(c->P, P.data(), P.size() * sizeof(float), cudaMemcpyHostToDevice));
+    USBS_CUDA_TRY(c, cudaMemcpyAsync(c->P, P.data(), P.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
   }
+  USBS_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   c->started = true;
   return USBS_OK;
 }
@@ -1072,7 +1075,9 @@ int usbs_grow(usbs_ctx* ctx_old, usbs_ctx** out, int64_t n, const int64_t* C_row
   cudaStreamSynchronize(c->stream);
   c->h_sc->f_y = c->alpha * std::max(c->h_lz->theta[0], 0.0) + by;
   c->h_sc->lam_max = c->h_lz->theta[0];
-  if ((e = cudaMemcpy(c->sc, c->h_sc, sizeof(DevScalars), cudaMemcpyHostToDevice))) return fail(e);
+  if ((e = cudaMemcpyAsync(c->sc, c->h_sc, sizeof(DevScalars), cudaMemcpyHostToDevice, c->stream)) ||
+      (e = cudaStreamSynchronize(c->stream)))
+    return fail(e);
   return USBS_OK;
 }
 

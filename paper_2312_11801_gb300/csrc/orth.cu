@@ -10,6 +10,9 @@
 //   finalize : out = (W - Q H2) R^-1                          (normalised new block)
 // Cross-CTA sums go to per-CTA FP64 partials in the same layout as before
 // ([b*64 + a*8 + c] for H_b[a][c]; [512 + a*8 + c] for the Gram matrix).
+#include <algorithm>
+#include <mutex>
+
 #include "common.cuh"
 
 namespace usbs {
@@ -365,15 +368,15 @@ size_t tile_smem(int nb, int extra) {
 
 template <typename T>
 void set_attrs() {
-  static bool done = false;
-  if (done) return;
-  const int mx = (int)tile_smem<T>(8, 8 * 64 + 64);
-  cudaFuncSetAttribute(k_tproj<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_tupdate<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_tfinalize<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_trestart<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)(sizeof(T) * (2 * (size_t)8 * TileRows<T>::value * 8 + JMAX * 32)));
-  done = true;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    const int mx = (int)tile_smem<T>(8, 8 * 64 + 64);
+    cudaFuncSetAttribute(k_tproj<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_tupdate<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_tfinalize<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_trestart<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(sizeof(T) * (2 * (size_t)8 * TileRows<T>::value * 8 + JMAX * 32)));
+  });
 }
 
 }  // namespace

@@ -4,6 +4,7 @@
 //  - the primal-dual interior point method of App. B.2 for eq. compressed_subprob_2,
 //  - the model value (App. B.1 in closed form), descent test and gates.
 #include <cfloat>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -1074,8 +1075,6 @@ __global__ void k_lanczos_reset(DevLanczos* lz) {
 
 }  // namespace
 
-static bool g_attr_done = false;
-
 // dynamic shared memory of k_ritz: A, V, T, Y (J x (J+1)) and T Y_keep (J x J/2), type S
 static size_t ritz_smem(size_t es, int J) { return es * (4 * J * (J + 1) + J * J / 2); }
 
@@ -1086,10 +1085,11 @@ static void ritz_attr() {
 }
 
 void small_init_attributes() {
-  if (g_attr_done) return;
-  ritz_attr<double, 16>(); ritz_attr<double, 32>(); ritz_attr<double, 64>();
-  ritz_attr<float, 16>(); ritz_attr<float, 32>(); ritz_attr<float, 64>();
-  g_attr_done = true;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    ritz_attr<double, 16>(); ritz_attr<double, 32>(); ritz_attr<double, 64>();
+    ritz_attr<float, 16>(); ritz_attr<float, 32>(); ritz_attr<float, 64>();
+  });
 }
 
 void launch_chol_block(Ctx* c, int j, int nb, int write_T, int is_resid, int defl_pass) {

@@ -52,6 +52,29 @@ class usbs_result(ctypes.Structure):
                 ("last", usbs_step_info)]
 
 
+class usbs_server_params(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_slots", ctypes.c_int),
+                ("cache_entries", ctypes.c_int), ("dry_run", ctypes.c_int),
+                ("solver", usbs_params)]
+
+
+class usbs_completion(ctypes.Structure):
+    _fields_ = [("request_id", ctypes.c_int64), ("parent_id", ctypes.c_int64),
+                ("status", ctypes.c_int), ("warm", ctypes.c_int), ("iters", ctypes.c_int),
+                ("slot", ctypes.c_int), ("objective", ctypes.c_double),
+                ("dual_bound", ctypes.c_double), ("relgap", ctypes.c_double),
+                ("relinf", ctypes.c_double), ("t_arrival", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_finish", ctypes.c_double),
+                ("bytes", ctypes.c_uint64)]
+
+
+class usbs_server_stats_t(ctypes.Structure):
+    _fields_ = [("used_bytes", ctypes.c_uint64), ("peak_bytes", ctypes.c_uint64),
+                ("budget_bytes", ctypes.c_uint64), ("pending", ctypes.c_int),
+                ("running", ctypes.c_int), ("peak_running", ctypes.c_int), ("cached", ctypes.c_int),
+                ("finished", ctypes.c_int64), ("rejected", ctypes.c_int64)]
+
+
 def _struct_dict(s):
     out = {}
     for name, _ in s._fields_:
@@ -96,6 +119,18 @@ SIGNATURES = [
     ("usbs_profile", ctypes.c_int, [_P, ctypes.c_int]),
     ("usbs_kernel_stats", ctypes.c_int, [_P, ctypes.c_int, _D, ctypes.POINTER(ctypes.c_longlong), _D]),
     ("usbs_launch_count", ctypes.c_longlong, [_P]),
+    ("usbs_instance_bytes", ctypes.c_uint64, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                              ctypes.c_int64, ctypes.c_int, ctypes.c_int]),
+    ("usbs_server_params_default", None, [ctypes.POINTER(usbs_server_params)]),
+    ("usbs_server_create", ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(usbs_server_params)]),
+    ("usbs_server_submit", ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _I64, _I32,
+                                          _D, ctypes.c_int64, ctypes.c_int64, _I32, _I32, _I32, _D, _D,
+                                          _U8, _F, ctypes.c_double, ctypes.c_double]),
+    ("usbs_server_poll", ctypes.c_int, [_P, ctypes.POINTER(usbs_completion), ctypes.c_int, ctypes.c_int]),
+    ("usbs_server_get_stats", ctypes.c_int, [_P, ctypes.POINTER(usbs_server_stats_t)]),
+    ("usbs_server_destroy", ctypes.c_int, [_P]),
+    ("usbs_batch_solve", ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                        ctypes.POINTER(usbs_result), ctypes.POINTER(ctypes.c_int)]),
     ("usbs_scaling", ctypes.c_int, [_P, _D, _D]),
     ("usbs_dims", ctypes.c_int, [_P, _I64, _I64, ctypes.POINTER(ctypes.c_int),
                                  ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -349,3 +384,82 @@ def usbs_sketch_update_static(n, r, V_dev, S_dev, Psi_dev, P_dev, eta, stream=No
         st = ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
     _check(load().usbs_sketch_update_static(int(n), int(r), _dev(V_dev), _dev(S_dev),
                                             _dev(Psi_dev), _dev(P_dev), float(eta), st), None)
+
+
+def usbs_instance_bytes(n, nnzC, m, nnzA, r=0, precision=PRECISION_MIXED):
+    return int(load().usbs_instance_bytes(n, nnzC, m, nnzA, r, precision))
+
+
+def usbs_server_params_default(**overrides):
+    p = usbs_server_params()
+    load().usbs_server_params_default(ctypes.byref(p))
+    solver = overrides.pop("solver", None)
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    for k, v in (solver or {}).items():
+        setattr(p.solver, k, v)
+    return p
+
+
+class Server:
+    """Owns one usbs_server (usbs_server_create / usbs_server_destroy)."""
+
+    def __init__(self, ptr, r):
+        self.ptr = ptr
+        self.r = r
+
+    def close(self):
+        if self.ptr:
+            load().usbs_server_destroy(self.ptr)
+            self.ptr = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def usbs_server_create(**params):
+    p = usbs_server_params_default(**params)
+    out = ctypes.c_void_p()
+    _check(load().usbs_server_create(ctypes.byref(out), ctypes.byref(p)), None)
+    return Server(out, p.solver.r)
+
+
+def usbs_server_submit(srv, request_id, prob, parent_id=-1, psi=None, tol=1e-3, fake_service_s=0.0):
+    rp, cc, cv, ac, ai, aj, av, b, iq = _problem_arrays(prob)
+    psi_a = None if psi is None else np.ascontiguousarray(psi, np.float32)
+    _check(load().usbs_server_submit(
+        srv.ptr, int(request_id), int(parent_id), prob.n, _ptr(rp, ctypes.c_int64),
+        _ptr(cc, ctypes.c_int32), _ptr(cv, ctypes.c_double), prob.m, len(ac), _ptr(ac, ctypes.c_int32),
+        _ptr(ai, ctypes.c_int32), _ptr(aj, ctypes.c_int32), _ptr(av, ctypes.c_double),
+        _ptr(b, ctypes.c_double), _ptr(iq, ctypes.c_uint8),
+        None if psi_a is None else _ptr(psi_a, ctypes.c_float), float(tol), float(fake_service_s)), None)
+
+
+def usbs_server_poll(srv, max_items=64, wait_ms=0):
+    buf = (usbs_completion * max_items)()
+    k = load().usbs_server_poll(srv.ptr, buf, max_items, int(wait_ms))
+    _check(min(k, 0), None)
+    return [_struct_dict(buf[i]) for i in range(k)]
+
+
+def usbs_server_get_stats(srv):
+    st = usbs_server_stats_t()
+    _check(load().usbs_server_get_stats(srv.ptr, ctypes.byref(st)), None)
+    return _struct_dict(st)
+
+
+def usbs_server_destroy(srv):
+    srv.close()
+
+
+def usbs_batch_solve(ctxs, tol=1e-3, max_concurrency=8):
+    n = len(ctxs)
+    arr = (ctypes.c_void_p * n)(*[c.ptr.value if isinstance(c.ptr, ctypes.c_void_p) else c.ptr for c in ctxs])
+    res = (usbs_result * n)()
+    st = (ctypes.c_int * n)()
+    rc = load().usbs_batch_solve(arr, n, float(tol), int(max_concurrency), res, st)
+    _check(rc, None, allow=(USBS_ENOTCONV,))
+    return [_struct_dict(res[i]) for i in range(n)], list(st)
