@@ -180,7 +180,8 @@ def run_ours(args, world, rank, local, pg):
     torch.cuda.set_device(dev)
     prob, psi = make_problem(args.side)
     stream = torch.cuda.Stream(device=dev)
-    params = dict(r=R_SKETCH, precision=U.PRECISION_MIXED, stream=stream, max_iters=args.max_iters)
+    params = dict(r=R_SKETCH, precision=U.PRECISION_MIXED, stream=stream, max_iters=args.max_iters,
+                  lanczos_basis=args.lanczos_basis, lanczos_tol=args.lanczos_tol)
     ctx = U.usbs_create(prob, psi=psi, **params)
 
     # warm-up solves (also give the iteration count of one solve)
@@ -254,6 +255,7 @@ def run_ours(args, world, rank, local, pg):
         "config": {"workload": WORKLOAD, "n": prob.n, "edges": 2 * SIDE * SIDE, "weights": "+-1",
                    "r": R_SKETCH, "k_c": 8, "rho": 0.01, "beta": 0.25, "tol": TOL,
                    "precision": "mixed: FP32 bulk, FP64 k-sized", "parallelism": f"replicas{world}",
+                   "lanczos_basis": args.lanczos_basis, "lanczos_tol": args.lanczos_tol or "default",
                    "l2": "inputs and basis larger than L2 (no flush)",
                    "iters_per_solve": iters, "converged": conv},
         "e2e": {"value": world * args.e2e_steps / e2e_elapsed, "unit": UNIT,
@@ -313,6 +315,8 @@ def main():
     ap.add_argument("--side", type=int, default=SIDE)
     ap.add_argument("--max-iters", type=int, default=2000)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--lanczos-basis", type=int, default=64, choices=[16, 32, 64])
+    ap.add_argument("--lanczos-tol", type=float, default=0.0, help="0 = the library default")
     ap.add_argument("--ref-iters", type=int, default=100,
                     help="iterations per solve used to scale the reference arm's sample")
     args = ap.parse_args()

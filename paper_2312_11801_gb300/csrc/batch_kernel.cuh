@@ -1,0 +1,371 @@
+// Batched USBS: many small instances solved by one persistent kernel launch.
+//
+// One CTA owns one instance at a time and runs its whole solve (cold start, then
+// Algorithm 1 iterations until both gates pass or max_iters) without returning to the
+// host: the same steps, in the same order, as usbs_solve on that context, built from the
+// same device bodies as the per-step kernels, each called with (cta, ncta) = (0, 1) so
+// that it covers every row of the instance and writes its final sums straight into the
+// context's reduction buffer.  Control flow that the per-step path takes on the host
+// (Lanczos restarts, deflation passes, the alternating maximisation, the gates) runs on
+// the device from the same flags.  CTAs take instances from an atomic counter, so a
+// launch of min(count, resident CTAs) CTAs drains any number of instances.
+//
+// Every loop is bounded by the instance's parameters (max_iters, lanczos_restarts,
+// max_alt, ipm_max_iter, the Jacobi sweep cap), and no CTA waits on another.
+//
+// Each instantiation (bulk type, basis size) is compiled in its own translation unit
+// (batch_*.cu), which must define USBS_PLAIN_LOADS before including this header: a
+// buffer written earlier in the launch must not be read through the read-only path.
+#pragma once
+#ifndef USBS_PLAIN_LOADS
+#error "define USBS_PLAIN_LOADS before including batch_kernel.cuh"
+#endif
+
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "common.cuh"
+#include "dev_bulk.cuh"
+#include "dev_orth.cuh"
+#include "dev_small.cuh"
+
+namespace usbs {
+
+// Device view of one context, filled from Ctx on the host; the kernel writes the
+// outputs at the end.
+struct BatchDesc {
+  // sizes and parameters
+  int n, m, nnz_off, kc, r, J, keep, has_offdiag_A, any_ineq;
+  int restarts, max_alt, ipm_max_iter, max_iters;
+  double alpha, rho, beta, bnorm, tol, lanczos_tol, ipm_mu_tol, alt_tol;
+  uint64_t seed, rng_counter;
+  // operator and constraints
+  const int* rowptr; const int* col; const double* valC64; void* valM; const void* valC;
+  const double* diagC64; void* dM; const void* dC;
+  const int* diag_ptr; const int* diag_con; const double* diag_val;
+  const int* slot_ptr; const int* slot_con; const double* slot_val;
+  const int* con_ptr; const int* ent_i; const int* ent_j; const void* ent_v;
+  const double* b; const uint8_t* ineq;
+  // iterate and work buffers
+  double* y; double* ycand; double* ax; double* axnew; double* nu;
+  void* V; void* Vnew; void* W; void* Q; void* Q2; float* P; const float* Psi;
+  DevScalars* sc; DevLanczos* lz; double* red;
+  // outputs
+  int iters, converged, descent_steps, status;
+  int v_swapped, ax_swapped, last_n_alt, last_matvecs;
+  long long matvecs;
+};
+
+namespace {
+
+constexpr int BT = 256;   // threads per CTA: the bodies are written for 8 warps
+
+template <typename T>
+struct BatchCtx {
+  BatchDesc* d;
+  T* Q;
+  T* Q2;
+  uint64_t rng;
+  long long matvecs;
+};
+
+template <typename T>
+__device__ void b_orth_block(BatchCtx<T>& b, T* Q, int nb, T* W, T* out, int j, int write_T,
+                             int is_resid) {
+  const BatchDesc* d = b.d;
+  const size_t bs = (size_t)d->n * 8;
+  double* red = d->red;
+  const double thr = sizeof(T) == 8 ? 1e-16 : 1e-6;
+  if (nb > 0) {
+    k_tproj_dev<T>(0, 1, d->n, Q, bs, nb, W, red + RED_H, nullptr);
+    __syncthreads();
+  }
+  k_tupdate_dev<T>(0, 1, d->n, Q, bs, nb, W, red + RED_H, red + RED_H2, nullptr);
+  __syncthreads();
+  k_chol_block_dev(d->lz, red, j, nb, write_T, is_resid, 0, thr);
+  __syncthreads();
+  k_tfinalize_dev<T>(0, 1, d->n, Q, bs, nb, W, red + RED_H2, d->lz, out, nullptr,
+                     d->seed + 0x1000003ull * (b.rng++));
+  __syncthreads();
+  const int* defl = &d->lz->defl;
+  const int* defl2 = &d->lz->defl2;
+  for (int pass = 1; pass <= 2; ++pass) {
+    const int* mask = pass == 1 ? defl : defl2;
+    if (nb > 0) {
+      k_tproj_dev<T>(0, 1, d->n, Q, bs, nb, out, red + RED_H, mask);
+      __syncthreads();
+    }
+    k_tupdate_dev<T>(0, 1, d->n, Q, bs, nb, out, red + RED_H, red + RED_H2, mask);
+    __syncthreads();
+    k_chol_block_dev(d->lz, red, j, nb, 0, is_resid, pass, thr);
+    __syncthreads();
+    k_tfinalize_dev<T>(0, 1, d->n, Q, bs, nb, out, red + RED_H2, d->lz, out, mask,
+                       d->seed + 0x2000011ull * (b.rng++));
+    __syncthreads();
+  }
+}
+
+// Top eigenpairs of C - A*(y): the device twin of the host Lanczos driver.  Returns 0 or
+// USBS_ENUMERIC.  start may be null (zero start block, replaced by random columns).
+template <typename T, typename S, int J>
+__device__ int b_lanczos(BatchCtx<T>& b, const double* y, const T* start, T* out_vecs) {
+  const BatchDesc* d = b.d;
+  const int n = d->n;
+  const size_t bs = (size_t)n * 8;
+  k_setup_diag_dev<T>(0, 1, n, d->diagC64, d->diag_ptr, d->diag_con, d->diag_val, y, (T*)d->dM);
+  if (d->has_offdiag_A && d->nnz_off > 0)
+    k_setup_off_dev<T>(0, 1, d->nnz_off, d->valC64, d->slot_ptr, d->slot_con, d->slot_val, y,
+                       (T*)d->valM);
+  k_lanczos_reset_dev(d->lz);
+  T* W = (T*)d->W;
+  for (size_t t = threadIdx.x; t < bs; t += blockDim.x) W[t] = start ? start[t] : (T)0;
+  __syncthreads();
+  const T* valM = (const T*)(d->has_offdiag_A ? d->valM : d->valC);
+  T* Q = b.Q;
+  T* Q2 = b.Q2;
+  b_orth_block<T>(b, Q, 0, W, Q, -1, 0, 0);
+  constexpr int nblk = J / 8, keep = J / 2;
+  const double jac_eps = sizeof(S) == 8 ? 1e-14 : 1e-5;
+  const int sweeps = sizeof(S) == 8 ? 30 : 12;
+  int nb0 = 0;
+  int rc = 0;
+  for (int cycle = 0; cycle < d->restarts; ++cycle) {
+    for (int j = nb0; j < nblk; ++j) {
+      k_spmm_dev<T>(0, 1, n, d->rowptr, d->col, valM, (const T*)d->dM, Q + j * bs, W);
+      __syncthreads();
+      b.matvecs += 8;
+      b_orth_block<T>(b, Q, j + 1, W, Q + (j + 1) * bs, j, 1, j == nblk - 1);
+    }
+    k_ritz_dev<S, J>(d->lz, d->kc, d->lanczos_tol, sweeps, jac_eps);
+    __syncthreads();
+    if (d->lz->status != 0) { rc = USBS_ENUMERIC; break; }
+    if (d->lz->converged || cycle == d->restarts - 1) break;
+    k_trestart_dev<T>(0, 1, n, Q, bs, nblk, keep / 8, d->lz->Y, Q2, bs, Q + nblk * bs, keep / 8);
+    __syncthreads();
+    T* t = Q; Q = Q2; Q2 = t;
+    nb0 = keep / 8;
+  }
+  b.Q = Q;
+  b.Q2 = Q2;
+  if (rc == 0) {
+    k_trestart_dev<T>(0, 1, n, Q, bs, nblk, 1, d->lz->Y, out_vecs, bs, nullptr, 0);
+    __syncthreads();
+  }
+  return rc;
+}
+
+// One USBS iteration (Algorithm 1), the device twin of the host step.
+template <typename T, typename S, int J>
+__device__ int b_step(BatchCtx<T>& b, T*& V, T*& Vnew, double*& ax, double*& axnew, int& n_alt_out) {
+  BatchDesc* d = b.d;
+  const int n = d->n, m = d->m;
+  DevScalars* sc = d->sc;
+  double* red = d->red;
+  k_begin_step_dev(sc);
+  // V^T C V
+  k_spmm_dev<T>(0, 1, n, d->rowptr, d->col, (const T*)d->valC, (const T*)d->dC, V, (T*)d->W);
+  __syncthreads();
+  k_tproj_dev<T>(0, 1, n, V, (size_t)n * 8, 1, (const T*)d->W, red + RED_VC, nullptr);
+  __syncthreads();
+  // [G | A Xbar | y - b/rho]^T [G | A Xbar | y - b/rho]
+  k_gstats_dev<T>(0, 1, m, d->con_ptr, d->ent_i, d->ent_j, (const T*)d->ent_v, V, ax, d->y, d->b,
+                  1.0 / d->rho, red + RED_AUG);
+  __syncthreads();
+  if (d->r) {
+    k_vt_psi_dev<T>(0, 1, n, d->r, V, d->Psi, red + RED_SK);
+    __syncthreads();
+  }
+  for (int c = threadIdx.x; c < m; c += blockDim.x) d->nu[c] = 0.0;
+  __syncthreads();
+  int n_alt;
+  for (n_alt = 1; n_alt <= d->max_alt; ++n_alt) {
+    k_ipm_dev(sc, red, d->kc, d->alpha, d->rho, d->ipm_mu_tol, d->ipm_max_iter, n_alt == 1);
+    __syncthreads();
+    if (!d->any_ineq) break;
+    k_alt_dev<T>(0, 1, m, d->con_ptr, d->ent_i, d->ent_j, (const T*)d->ent_v, V, sc, ax, d->y,
+                 d->b, d->ineq, d->rho, d->alpha, d->nu, red + RED_VEC);
+    __syncthreads();
+    const double dn2 = red[RED_VEC + 37];
+    if (sqrt(fmax(dn2, 0.0)) <= d->alt_tol * (1.0 + d->bnorm)) break;
+  }
+  n_alt_out = min(n_alt, d->max_alt);
+  // candidate y~ and A X_{t+1}; the single CTA writes the max |d| to slot 39 itself
+  k_xupdate_dev<T>(0, 1, m, d->con_ptr, d->ent_i, d->ent_j, (const T*)d->ent_v, V, sc, ax, d->y,
+                   d->b, d->ineq, 1.0 / d->rho, axnew, d->ycand, red + RED_VEC);
+  __syncthreads();
+  const long long mv0 = b.matvecs;
+  const int rc = b_lanczos<T, S, J>(b, d->ycand, V, Vnew);
+  d->last_matvecs = (int)(b.matvecs - mv0);
+  if (rc) return rc;
+  if (threadIdx.x < 32) k_finish_dev(sc, d->lz, red, d->kc, d->alpha, d->beta, d->bnorm);
+  __syncthreads();
+  k_commit_dev(0, 1, m, sc, d->ycand, d->y);
+  if (d->r)
+    k_sketch_update_dev<T>(0, 1, n, d->r, V, sc->S, red + RED_SK, d->P, &sc->eta, 0.0);
+  __syncthreads();
+  T* t = V; V = Vnew; Vnew = t;
+  double* u = ax; ax = axnew; axnew = u;
+  if (threadIdx.x == 0) sc->n_alt = n_alt_out;
+  __syncthreads();
+  return sc->status != 0 ? USBS_ENUMERIC : 0;
+}
+
+template <typename T, typename S, int J>
+__global__ void __launch_bounds__(BT) k_batch_solve(BatchDesc* descs, int count, int* next) {
+  __shared__ int slot;
+  for (;;) {
+    if (threadIdx.x == 0) slot = atomicAdd(next, 1);
+    __syncthreads();
+    const int i = slot;
+    __syncthreads();
+    if (i >= count) return;
+    BatchDesc* d = descs + i;
+    BatchCtx<T> b{d, (T*)d->Q, (T*)d->Q2, d->rng_counter, 0};
+    T* V = (T*)d->V;
+    T* Vnew = (T*)d->Vnew;
+    double* ax = d->ax;
+    double* axnew = d->axnew;
+    const int n = d->n, m = d->m;
+    // cold start: y = 0, A Xbar = 0, P = 0, V = 0, then V from an eigen solve at y = 0
+    for (int c = threadIdx.x; c < m; c += blockDim.x) { d->y[c] = 0.0; ax[c] = 0.0; }
+    for (size_t t = threadIdx.x; t < (size_t)n * d->r; t += blockDim.x) d->P[t] = 0.f;
+    for (size_t t = threadIdx.x; t < (size_t)n * 8; t += blockDim.x) V[t] = (T)0;
+    __syncthreads();
+    int rc = b_lanczos<T, S, J>(b, d->y, V, Vnew);
+    int iters = 0, conv = 0, desc = 0, n_alt = 0;
+    if (rc == 0) {
+      T* t = V; V = Vnew; Vnew = t;
+      k_cold_dev(d->sc, d->lz, d->alpha);
+      __syncthreads();
+      for (int it = 0; it < d->max_iters; ++it) {
+        rc = b_step<T, S, J>(b, V, Vnew, ax, axnew, n_alt);
+        if (rc) break;
+        ++iters;
+        desc += d->sc->descent;
+        if (d->sc->relgap <= d->tol && d->sc->relinf <= d->tol) { conv = 1; break; }
+      }
+    }
+    if (threadIdx.x == 0) {
+      d->iters = iters;
+      d->converged = conv;
+      d->descent_steps = desc;
+      d->status = rc;
+      d->v_swapped = (V != (T*)d->V) ? 1 : 0;
+      d->ax_swapped = (ax != d->ax) ? 1 : 0;
+      d->last_n_alt = n_alt;
+      d->matvecs = b.matvecs;
+      d->rng_counter = b.rng;
+      // the Lanczos buffers may have traded places: report which is which
+      d->Q = b.Q;
+      d->Q2 = b.Q2;
+    }
+    __syncthreads();
+  }
+}
+
+// dynamic shared memory of one batched CTA: the largest of the bodies' needs
+template <typename T>
+size_t batch_smem(int J) {
+  constexpr int TR = sizeof(T) == 8 ? 64 : 128;
+  const int nbmax = J / 8;   // projections run against at most J/8 blocks
+  size_t m = 0;
+  m = std::max(m, sizeof(T) * (2 * (size_t)(nbmax + 1) * TR * 8 + 8 * 64 + 64));  // tiles
+  m = std::max(m, sizeof(double) * 8 * 576);                                      // epilogues
+  m = std::max(m, sizeof(T) * (2 * (size_t)nbmax * TR * 8 + (size_t)J * (J / 2)));  // restart
+  m = std::max(m, sizeof(T) * (4 * (size_t)J * (J + 1) + (size_t)J * J / 2));       // Ritz
+  m = std::max(m, sizeof(T) * 128 * AUG + sizeof(double) * 4 * 880);              // gstats
+  return m;
+}
+
+template <typename T, typename S, int J>
+int launch_batch(const std::vector<Ctx*>& cs, cudaStream_t st, double tol, std::string& err) {
+  const int count = (int)cs.size();
+  std::vector<BatchDesc> h(count);
+  for (int i = 0; i < count; ++i) {
+    const Ctx* c = cs[i];
+    BatchDesc& d = h[i];
+    std::memset(&d, 0, sizeof(d));
+    d.n = (int)c->n; d.m = (int)c->m; d.nnz_off = c->nnz_off; d.kc = c->kc; d.r = c->r;
+    d.J = c->J; d.keep = c->keep; d.has_offdiag_A = c->has_offdiag_A; d.any_ineq = c->any_ineq;
+    d.restarts = c->prm.lanczos_restarts; d.max_alt = c->prm.max_alt;
+    d.ipm_max_iter = c->prm.ipm_max_iter; d.max_iters = c->prm.max_iters;
+    d.tol = tol;
+    d.alpha = c->alpha; d.rho = c->prm.rho; d.beta = c->prm.beta; d.bnorm = c->bnorm;
+    d.lanczos_tol = c->prm.lanczos_tol; d.ipm_mu_tol = c->prm.ipm_mu_tol; d.alt_tol = c->prm.alt_tol;
+    d.seed = c->seed; d.rng_counter = c->rng_counter;
+    d.rowptr = c->rowptr; d.col = c->col; d.valC64 = c->valC64; d.valM = c->valM; d.valC = c->valC;
+    d.diagC64 = c->diagC64; d.dM = c->dM; d.dC = c->dC;
+    d.diag_ptr = c->diag_ptr; d.diag_con = c->diag_con; d.diag_val = c->diag_val;
+    d.slot_ptr = c->slot_ptr; d.slot_con = c->slot_con; d.slot_val = c->slot_val;
+    d.con_ptr = c->con_ptr; d.ent_i = c->ent_i; d.ent_j = c->ent_j; d.ent_v = c->ent_v;
+    d.b = c->b; d.ineq = c->ineq;
+    d.y = c->y; d.ycand = c->ycand; d.ax = c->ax; d.axnew = c->axnew; d.nu = c->nu;
+    d.V = c->V; d.Vnew = c->Vnew; d.W = c->W; d.Q = c->Q; d.Q2 = c->Q2; d.P = c->P; d.Psi = c->Psi;
+    d.sc = c->sc; d.lz = c->lz; d.red = c->red;
+  }
+  BatchDesc* dd = nullptr;
+  int* dnext = nullptr;
+  auto fail = [&](cudaError_t e, const char* what) {
+    err = std::string(what) + ": " + cudaGetErrorString(e);
+    if (dd) cudaFree(dd);
+    if (dnext) cudaFree(dnext);
+    return USBS_ECUDA;
+  };
+  cudaError_t e;
+  if ((e = cudaMalloc(&dd, sizeof(BatchDesc) * count))) return fail(e, "cudaMalloc");
+  if ((e = cudaMalloc(&dnext, sizeof(int)))) return fail(e, "cudaMalloc");
+  if ((e = cudaMemcpyAsync(dd, h.data(), sizeof(BatchDesc) * count, cudaMemcpyHostToDevice, st)))
+    return fail(e, "descriptor upload");
+  if ((e = cudaMemsetAsync(dnext, 0, sizeof(int), st))) return fail(e, "cudaMemsetAsync");
+  const size_t smem = batch_smem<T>(J);
+  static std::once_flag once;
+  std::call_once(once, [&] {
+    cudaFuncSetAttribute(k_batch_solve<T, S, J>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+  });
+  int per_sm = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_solve<T, S, J>, BT, smem)))
+    return fail(e, "occupancy");
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = std::max(1, std::min(count, std::max(per_sm, 1) * sms));
+  k_batch_solve<T, S, J><<<grid, BT, smem, st>>>(dd, count, dnext);
+  if ((e = cudaGetLastError())) return fail(e, "k_batch_solve launch");
+  if ((e = cudaMemcpyAsync(h.data(), dd, sizeof(BatchDesc) * count, cudaMemcpyDeviceToHost, st)))
+    return fail(e, "descriptor download");
+  if ((e = cudaStreamSynchronize(st))) return fail(e, "k_batch_solve");
+  cudaFree(dd);
+  cudaFree(dnext);
+  for (int i = 0; i < count; ++i) {
+    Ctx* c = cs[i];
+    const BatchDesc& d = h[i];
+    if (d.v_swapped) std::swap(c->V, c->Vnew);
+    if (d.ax_swapped) std::swap(c->ax, c->axnew);
+    c->Q = d.Q;
+    c->Q2 = d.Q2;
+    c->rng_counter = d.rng_counter;
+    c->total_matvecs += d.matvecs;
+    c->started = d.status == USBS_OK;
+  }
+  // results are read back by the caller from each context
+  for (int i = 0; i < count; ++i) {
+    Ctx* c = cs[i];
+    c->batch_iters = h[i].iters;
+    c->batch_converged = h[i].converged;
+    c->batch_descent = h[i].descent_steps;
+    c->batch_status = h[i].status;
+    c->batch_matvecs = h[i].matvecs;
+    c->batch_last_matvecs = h[i].last_matvecs;
+    c->batch_n_alt = h[i].last_n_alt;
+  }
+  return USBS_OK;
+}
+
+}  // namespace
+
+}  // namespace usbs

@@ -11,6 +11,18 @@
 
 #include "usbs.h"
 
+// Read-only qualifiers of the kernel bodies.  A kernel that writes a buffer and reads it
+// again later in the same launch (the batched solver runs a whole solve in one launch)
+// must not read it through the non-coherent read-only path, so that translation unit
+// defines USBS_PLAIN_LOADS before including this header.
+#ifdef USBS_PLAIN_LOADS
+#define USBS_RESTRICT
+#define USBS_LDG(p) (*(p))
+#else
+#define USBS_RESTRICT __restrict__
+#define USBS_LDG(p) __ldg(p)
+#endif
+
 namespace usbs {
 
 constexpr int KB = 8;            // Lanczos block width and max k_c (V is n x 8, zero-padded)
@@ -143,7 +155,20 @@ struct Ctx {
   struct PendingEv { cudaEvent_t a, b; int kind; };
   std::vector<PendingEv> prof_pending;
   std::vector<cudaEvent_t> ev_pool;
+  // outcome of the last batched solve of this context (batch.cu)
+  int batch_iters = 0, batch_converged = 0, batch_descent = 0, batch_status = 0;
+  int batch_last_matvecs = 0, batch_n_alt = 0;
+  long long batch_matvecs = 0;
 };
+
+// ---- batched solver (batch.cu) -------------------------------------------------------------
+// A context the persistent batched kernel can solve (its basis size is instantiated and
+// no per-step host work is enabled).
+bool batch_eligible(const Ctx* c);
+// Cold-start solves of all contexts (same precision and basis) in one launch on stream st.
+int batch_run(const std::vector<Ctx*>& cs, cudaStream_t st, double tol, std::string& err);
+// usbs_result of a context's last batched solve, as usbs_solve would report it.
+int batch_result(Ctx* c, usbs_result* out);
 
 void prof_resolve(Ctx* c);
 
@@ -217,12 +242,6 @@ int check_launch(Ctx* c, const char* what);
 template <typename T> struct Bulk {
   static void setup_operator(Ctx* c, const double* y);
   static void spmm(Ctx* c, const void* valM, const void* dM, const void* X, void* Y);
-  static void proj(Ctx* c, const void* Qb, int nb, const void* W, int nparts, const int* mask);
-  static void update_proj(Ctx* c, const void* Qb, int nb, void* W, int nparts, const int* mask);
-  static void finalize(Ctx* c, const void* Qb, int nb, const void* W, void* out, int nparts,
-                       const int* mask, uint64_t seed);
-  static void restart_gemm(Ctx* c, const void* Qb, int J, int nout_blocks, const double* Y,
-                           void* out, const void* resid, int resid_slot);
   static void gstats(Ctx* c, const void* V, const double* ax, const double* y, int nparts);
   static void alt_pass(Ctx* c, const void* V, int nparts);
   static void xupdate(Ctx* c, const void* V, int nparts);
@@ -230,7 +249,6 @@ template <typename T> struct Bulk {
   static void sketch_update(Ctx* c, const void* V, const double* S, const double* Bsk, float* P,
                             const float* Psi, const double* eta_dev, double eta_host);
   static void constraint_eval(Ctx* c, const void* V, const double* S, double* z);
-  static void gram_xy(Ctx* c, const void* X, const void* Y, int nparts);
 };
 
 // shared-memory-staged block Gram-Schmidt kernels (orth.cu); grid = orth_grid(c, n)
@@ -241,6 +259,8 @@ template <typename T> struct Orth {
                        uint64_t seed);
   static void restart(Ctx* c, const void* Qb, int J, int nout, const double* Y, void* out,
                       const void* resid, int resid_slot);
+  // X^T Y of two n x 8 blocks (partials in the layout of proj with one block)
+  static void gram_xy(Ctx* c, const void* X, const void* Y);
 };
 int orth_grid(Ctx* c, int64_t rows);
 

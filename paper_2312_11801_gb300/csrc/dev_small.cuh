@@ -1,0 +1,1001 @@
+// Device bodies of the k-sized single-CTA kernels of a USBS iteration (FP64 unless
+// stated): Cholesky-QR of a Lanczos block with deflation, Rayleigh-Ritz by parallel
+// Jacobi, the App. B.2 interior point method, and the model value, descent test and
+// gates.  Each __global__ kernel in small.cu calls one body; the batched solver calls
+// them in sequence inside its own CTA.
+#pragma once
+
+#include <cfloat>
+
+#include "common.cuh"
+
+namespace usbs {
+namespace {
+
+__device__ __forceinline__ int svec_idx(int p, int q, int k) {  // p >= q, k x k matrix
+  return q * k - (q * (q - 1)) / 2 + (p - q);
+}
+__device__ __forceinline__ int svec_idx8(int p, int q) { return svec_idx(p, q, 8); }
+
+constexpr double SQ2 = 1.41421356237309504880;
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// Warp-cooperative Cholesky A = R^T R (R upper) of a k x k matrix, k <= 8, row stride 8.
+// All 32 lanes call it; lane l < k keeps column l of R.  Returns false (on every lane)
+// if a pivot is not positive.  When R is non-null the factor is stored (row stride 8).
+__device__ bool warp_chol(const double* A, double* R, int k) {
+  const int lane = threadIdx.x & 31;
+  double rc[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) rc[i] = 0.0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    if (j >= k) break;
+    double d = 0.0;
+    if (lane == j) {
+      d = A[j * 8 + j];
+#pragma unroll
+      for (int l = 0; l < 8; ++l)
+        if (l < j) d -= rc[l] * rc[l];
+    }
+    d = __shfl_sync(FULL, d, j);
+    if (!(d > 0.0)) return false;
+    const double rjj = sqrt(d), inv = 1.0 / rjj;
+    double sacc = (lane > j && lane < k) ? A[j * 8 + lane] : 0.0;
+#pragma unroll
+    for (int l = 0; l < 8; ++l) {
+      if (l < j) {
+        const double rlj = __shfl_sync(FULL, rc[l], j);
+        sacc -= rlj * rc[l];
+      }
+    }
+    if (lane == j) rc[j] = rjj;
+    else if (lane > j && lane < k) rc[j] = sacc * inv;
+  }
+  if (R && lane < 8) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) R[i * 8 + lane] = (i <= lane && lane < k) ? rc[i] : 0.0;
+  }
+  __syncwarp();
+  return true;
+}
+
+// Inverse of an SPD k x k matrix from its upper Cholesky factor R (row stride 8):
+// A^-1 = R^-1 R^-T.  Warp-cooperative; Rinv is scratch (row stride 8).
+__device__ void warp_spd_inverse(const double* R, double* Rinv, double* Ainv, int k) {
+  const int lane = threadIdx.x & 31;
+  if (lane < k) {
+    const int c = lane;
+    double x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = 0.0;
+    x[c] = 1.0 / R[c * 8 + c];
+    for (int i = c - 1; i >= 0; --i) {
+      double sacc = 0.0;
+      for (int l = i + 1; l <= c; ++l) sacc += R[i * 8 + l] * x[l];
+      x[i] = -sacc / R[i * 8 + i];
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) Rinv[i * 8 + c] = (i < k) ? x[i] : 0.0;
+  }
+  __syncwarp();
+  for (int t = lane; t < 64; t += 32) {
+    const int i = t / 8, j = t % 8;
+    double v = 0.0;
+    if (i < k && j < k)
+      for (int l = 0; l < k; ++l) v += Rinv[i * 8 + l] * Rinv[j * 8 + l];
+    Ainv[t] = v;
+  }
+  __syncwarp();
+}
+
+// Largest eigenvalue of a small symmetric matrix (k <= 8, row stride 8): parallel
+// Jacobi in FP32 by one warp for the eigenvector, then its FP64 Rayleigh quotient.
+__device__ double warp_lambda_max(const double* A, int k, float* Af, float* Vf) {
+  const int lane = threadIdx.x & 31;
+  for (int t = lane; t < 64; t += 32) {
+    const int i = t / 8, j = t % 8;
+    Af[t] = (i < k && j < k) ? (float)A[t] : (i == j ? -1e30f : 0.f);
+    Vf[t] = (i == j) ? 1.f : 0.f;
+  }
+  __syncwarp();
+  for (int sweep = 0; sweep < 12; ++sweep) {
+    for (int round = 0; round < 7; ++round) {
+      // circle ordering on 8 indices
+      float c = 1.f, sv = 0.f;
+      int p = 0, q = 0;
+      if (lane < 4) {
+        const int pa = lane == 0 ? 0 : 1 + ((lane - 1 + round) % 7);
+        const int pb = 1 + ((7 - lane - 1 + round) % 7);
+        p = min(pa, pb); q = max(pa, pb);
+        const float apq = Af[p * 8 + q];
+        if (fabsf(apq) > 1e-30f) {
+          const float tau = (Af[q * 8 + q] - Af[p * 8 + p]) / (2.f * apq);
+          const float t = fabsf(tau) > 1e18f ? 0.5f / tau
+                                              : (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(tau * tau + 1.f));
+          c = 1.f / sqrtf(t * t + 1.f);
+          sv = t * c;
+        }
+      }
+      float cs[4], sn[4];
+      int pp[4], qq[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        cs[u] = __shfl_sync(FULL, c, u);
+        sn[u] = __shfl_sync(FULL, sv, u);
+        pp[u] = __shfl_sync(FULL, p, u);
+        qq[u] = __shfl_sync(FULL, q, u);
+      }
+      __syncwarp();
+      float na = 0.f, nb = 0.f, nc = 0.f, nd = 0.f;
+      int k1 = 0, k2 = 0;
+      if (lane < 16) {
+        k1 = lane / 4; k2 = lane % 4;
+        const float a = Af[pp[k1] * 8 + pp[k2]], b = Af[pp[k1] * 8 + qq[k2]];
+        const float cc = Af[qq[k1] * 8 + pp[k2]], d = Af[qq[k1] * 8 + qq[k2]];
+        const float ra = cs[k1] * a - sn[k1] * cc, rb = cs[k1] * b - sn[k1] * d;
+        const float rcc = sn[k1] * a + cs[k1] * cc, rd = sn[k1] * b + cs[k1] * d;
+        na = cs[k2] * ra - sn[k2] * rb; nb = sn[k2] * ra + cs[k2] * rb;
+        nc = cs[k2] * rcc - sn[k2] * rd; nd = sn[k2] * rcc + cs[k2] * rd;
+      }
+      float vp = 0.f, vq = 0.f;
+      const int kr = lane / 8, row = lane % 8;
+      vp = Vf[row * 8 + pp[kr]];
+      vq = Vf[row * 8 + qq[kr]];
+      __syncwarp();
+      if (lane < 16) {
+        Af[pp[k1] * 8 + pp[k2]] = na; Af[pp[k1] * 8 + qq[k2]] = nb;
+        Af[qq[k1] * 8 + pp[k2]] = nc; Af[qq[k1] * 8 + qq[k2]] = nd;
+      }
+      Vf[row * 8 + pp[kr]] = cs[kr] * vp - sn[kr] * vq;
+      Vf[row * 8 + qq[kr]] = sn[kr] * vp + cs[kr] * vq;
+      __syncwarp();
+    }
+  }
+  // top eigenvector, FP64 Rayleigh quotient
+  int best = 0;
+  for (int i = 1; i < k; ++i)
+    if (Af[i * 8 + i] > Af[best * 8 + best]) best = i;
+  double num = 0.0, den = 0.0;
+  if (lane < k) {
+    const double vi = (double)Vf[lane * 8 + best];
+    double av = 0.0;
+    for (int j = 0; j < k; ++j) av += A[lane * 8 + j] * (double)Vf[j * 8 + best];
+    num = vi * av;
+    den = vi * vi;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    num += __shfl_xor_sync(FULL, num, o);
+    den += __shfl_xor_sync(FULL, den, o);
+  }
+  return num / den;
+}
+
+// ---- Cholesky-QR factor of a new block ------------------------------------------------------
+// red + RED_H: H (nb blocks x 64), red + RED_H2: H2 (nb x 64), red + RED_GRAM: W'^T W'.
+// Gram of the final block: W'^T W' - sum_b H2_b^T H2_b (the correction W' - Q H2 is
+// orthogonal to Q).  A column whose squared norm after orthogonalisation falls below
+// rel_thr times its squared norm before it is deficient: it is replaced by a random
+// vector (k_finalize) and the block is orthogonalised once more (the masked pass).
+// pass 0: the new block (writes T, R_last, and the second pass's mask); pass 1: masked by
+// defl, replaces still-dependent columns again and sets the third pass's mask; pass 2:
+// masked by defl2, zeroes what is still dependent.
+__device__ __forceinline__ void k_chol_block_dev(DevLanczos* lz, const double* USBS_RESTRICT red, int j, int nb,
+                             int write_T, int is_resid, int defl_pass, double rel_thr) {
+  if (defl_pass == 1 && lz->defl == 0) return;
+  if (defl_pass == 2 && lz->defl2 == 0) return;
+  __shared__ double G[64], pre[8], R[64], Ri[64];
+  __shared__ int dc[8];
+  const double* H = red + RED_H;
+  const double* H2 = red + RED_H2;
+  const double* Gram = red + RED_GRAM;
+  const int tid = threadIdx.x;
+  if (write_T && !defl_pass) {
+    for (int t = tid; t < nb * 64; t += blockDim.x) {
+      const int b = t / 64, a = (t / 8) % 8, cc = t % 8;
+      const int row = b * 8 + a, colT = j * 8 + cc;
+      if (b == j) {
+        const int tt = b * 64 + cc * 8 + a;
+        lz->T[row * JMAX + colT] = 0.5 * (H[t] + H2[t] + H[tt] + H2[tt]);
+      } else {
+        const double v = H[t] + H2[t];
+        lz->T[row * JMAX + colT] = v;
+        lz->T[colT * JMAX + row] = v;
+      }
+    }
+  }
+  if (tid < 64) {
+    const int a = tid / 8, cc = tid % 8;
+    double g = Gram[tid];
+    for (int b = 0; b < nb; ++b)
+      for (int r = 0; r < 8; ++r) g -= H2[b * 64 + r * 8 + a] * H2[b * 64 + r * 8 + cc];
+    G[tid] = g;
+  }
+  __syncthreads();
+  __shared__ double premax;
+  if (tid < 8) {
+    double p = G[tid * 8 + tid];
+    for (int b = 0; b < nb; ++b)
+      for (int r = 0; r < 8; ++r) {
+        const double h = H[b * 64 + r * 8 + tid] + H2[b * 64 + r * 8 + tid];
+        p += h * h;
+      }
+    pre[tid] = p;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double m = 0.0;
+    for (int a = 0; a < 8; ++a) m = fmax(m, pre[a]);
+    premax = m;
+  }
+  __syncthreads();
+  if (tid < 32) {
+    // warp-cooperative Cholesky with deficient columns: lane l owns column l of R
+    const int lane = tid;
+    double rc[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) rc[i] = 0.0;
+    int badmask = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      double d = 0.0;
+      if (lane == j) {
+        d = G[j * 8 + j];
+#pragma unroll
+        for (int l = 0; l < 8; ++l)
+          if (l < j) d -= rc[l] * rc[l];
+      }
+      d = __shfl_sync(FULL, d, j);
+      // deficient: small against the column's own norm before orthogonalisation, or
+      // against the block's largest column (a residual at rounding level)
+      const bool bad = !(d > rel_thr * pre[j]) || !(d > rel_thr * rel_thr * premax) || !(pre[j] > 0.0);
+      if (bad) {
+        badmask |= 1 << j;
+        if (lane == j) rc[j] = 1.0;   // row j of R stays e_j^T: the column is replaced
+        continue;
+      }
+      const double rjj = sqrt(d), inv = 1.0 / rjj;
+      double sacc = (lane > j && lane < 8) ? G[j * 8 + lane] : 0.0;
+#pragma unroll
+      for (int l = 0; l < 8; ++l) {
+        if (l < j) {
+          const double rlj = __shfl_sync(FULL, rc[l], j);
+          sacc -= rlj * rc[l];
+        }
+      }
+      if (lane == j) rc[j] = rjj;
+      else if (lane > j && lane < 8) rc[j] = sacc * inv;
+    }
+    if (lane < 8) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) R[i * 8 + lane] = (i <= lane) ? rc[i] : 0.0;
+    }
+    __syncwarp();
+    // column c of R^-1 by back substitution (lane c)
+    if (lane < 8) {
+      const int cidx = lane;
+      double x[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) x[i] = 0.0;
+      x[cidx] = 1.0 / R[cidx * 8 + cidx];
+      for (int i = cidx - 1; i >= 0; --i) {
+        double sacc = 0.0;
+        for (int l = i + 1; l <= cidx; ++l) sacc += R[i * 8 + l] * x[l];
+        x[i] = -sacc / R[i * 8 + i];
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i) Ri[i * 8 + cidx] = x[i];
+      const int isbad = (badmask >> lane) & 1;
+      dc[lane] = isbad ? (defl_pass < 2 ? 1 : 2) : 0;
+    }
+    __syncwarp();
+    for (int u = lane; u < 64; u += 32) {
+      lz->R[u] = R[u];
+      lz->Rinv[u] = Ri[u];
+      const int i = u / 8, jj = u % 8;
+      if (is_resid && defl_pass == 0)
+        lz->Rlast[u] = (i == jj && dc[i]) ? 0.0 : R[u];   // deficient rows carry no residual
+      else if (is_resid && defl_pass == 2 && dc[i])
+        lz->Rlast[u] = 0.0;                              // zeroed columns carry none either
+    }
+    if (lane < 8) lz->dcol[lane] = dc[lane];
+    // each masked pass reads its flag in every one of its kernels, so a flag is only
+    // changed by the pass before it
+    if (lane == 0) {
+      if (defl_pass == 0) {
+        lz->defl = (badmask != 0) ? 1 : 0;
+        lz->defl2 = 0;
+      } else if (defl_pass == 1) {
+        lz->defl2 = (badmask != 0) ? 1 : 0;
+      }
+    }
+  }
+}
+
+// ---- Rayleigh-Ritz: eigen-decomposition of T by parallel cyclic Jacobi ------------------------
+// S is the arithmetic of the whole Ritz step (FP32 in mixed mode, where GB300's FP64 rate
+// would make this one CTA the bottleneck; FP64 in the plain mode).  The J/2 rotations
+// of a round act on disjoint index pairs (circle ordering), so every 2 x 2 block
+// (p1, q1) x (p2, q2) of A is updated in one pass as R1^T [a b; c d] R2.  After the
+// sort, the kept Ritz vectors are orthonormalised (classical Gram-Schmidt, two passes)
+// and the restarted projected matrix is Y_keep^T T Y_keep, so rounding in the
+// rotations does not leak into the next cycle.
+template <typename S, int J>
+__device__ __forceinline__ void k_ritz_dev(DevLanczos* lz, int kc, double tol, int max_sweeps,
+                                              double jac_eps) {
+  constexpr int keep = J / 2;
+  constexpr int half = J / 2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int LD = J + 1;
+  S* A = reinterpret_cast<S*>(smem_raw);      // J x LD: T, rotated in place
+  S* Vv = A + J * LD;                           // J x LD: accumulated rotations
+  S* Tc = Vv + J * LD;                          // J x LD: copy of T
+  S* Y = Tc + J * LD;                           // J x LD: sorted Ritz vectors
+  S* Z = Y + J * LD;                            // J x keep: T Y_keep
+  __shared__ S cs[JMAX / 2], sn[JMAX / 2];
+  __shared__ int pp[JMAX / 2], qq[JMAX / 2];
+  __shared__ double th[JMAX];
+  __shared__ int order[JMAX];
+  __shared__ double wred[2][16];
+  __shared__ S hbuf[JMAX];
+  __shared__ S nrm;
+  __shared__ int stop, bad;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nw = blockDim.x >> 5;
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int t = tid; t < J * J; t += blockDim.x) {
+    const int i = t / J, j = t % J;
+    const double x = lz->T[i * JMAX + j];
+    if (!isfinite(x)) bad = 1;
+    A[i * LD + j] = (S)x;
+    Tc[i * LD + j] = (S)x;
+    Vv[i * LD + j] = (S)(i == j ? 1.0 : 0.0);
+  }
+  __syncthreads();
+  if (bad) {
+    // non-finite projected matrix: report it and stop the eigen solve
+    if (tid == 0) {
+      lz->status = USBS_ENUMERIC;
+      lz->converged = 1;
+      lz->cycles += 1;
+    }
+    for (int t = tid; t < JMAX * JMAX; t += blockDim.x) lz->Y[t] = ((t / JMAX) == (t % JMAX)) ? 1.0 : 0.0;
+    if (tid < JMAX) lz->theta[tid] = 0.0;
+    return;
+  }
+  const S skip = (S)(jac_eps * 1e-2), big = (S)1e18;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int t = tid; t < J * J; t += blockDim.x) {
+      const int i = t / J, j = t % J;
+      const double x = (double)A[i * LD + j];
+      tot += x * x;
+      if (i != j) off += x * x;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    }
+    if (lane == 0) { wred[0][warp] = off; wred[1][warp] = tot; }
+    __syncthreads();
+    if (tid == 0) {
+      double o2 = 0.0, t2 = 0.0;
+      for (int w = 0; w < nw; ++w) { o2 += wred[0][w]; t2 += wred[1][w]; }
+      stop = (o2 <= jac_eps * jac_eps * t2) ? 1 : 0;
+    }
+    __syncthreads();
+    if (stop) break;
+    if (tid == 0) lz->sweeps += 1;
+    for (int round = 0; round < J - 1; ++round) {
+      if (tid < half) {
+        // circle method: position 0 fixed, the others rotate
+        const int k = tid;
+        const int posA = k, posB = J - 1 - k;
+        const int pa = posA == 0 ? 0 : 1 + ((posA - 1 + round) % (J - 1));
+        const int pb = 1 + ((posB - 1 + round) % (J - 1));
+        const int p = min(pa, pb), q = max(pa, pb);
+        pp[k] = p;
+        qq[k] = q;
+        const S apq = A[p * LD + q];
+        S c = (S)1, sv = (S)0;
+        const S app = A[p * LD + p], aqq = A[q * LD + q];
+        // all in S: an FP64 sqrt here would be a long FP64 sequence every round
+        if (apq != (S)0 && fabs(apq) > skip * sqrt(fabs(app * aqq))) {
+          const S tau = (aqq - app) / ((S)2 * apq);
+          S t;
+          if (fabs(tau) > big) t = (S)0.5 / tau;
+          else t = (tau >= (S)0 ? (S)1 : (S)-1) / (fabs(tau) + sqrt(tau * tau + (S)1));
+          c = (S)1 / sqrt(t * t + (S)1);
+          sv = t * c;
+        }
+        cs[k] = c;
+        sn[k] = sv;
+      }
+      __syncthreads();
+      // A <- G^T A G on 2 x 2 blocks; V <- V G (index arithmetic on powers of two)
+      constexpr int NBLK = half * half, NITEM = half * half + J * half;
+      for (int t = tid; t < NITEM; t += blockDim.x) {
+        if (t < NBLK) {
+          const int k1 = t / half, k2 = t % half;
+          const int p1 = pp[k1], q1 = qq[k1], p2 = pp[k2], q2 = qq[k2];
+          const S c1 = cs[k1], s1 = sn[k1], c2 = cs[k2], s2 = sn[k2];
+          const S a = A[p1 * LD + p2], b = A[p1 * LD + q2];
+          const S cc = A[q1 * LD + p2], d = A[q1 * LD + q2];
+          // rows: [p1; q1] <- [c1 -s1; s1 c1] [p1; q1]
+          const S ra = c1 * a - s1 * cc, rb = c1 * b - s1 * d;
+          const S rc = s1 * a + c1 * cc, rd = s1 * b + c1 * d;
+          // cols: [p2 q2] <- [p2 q2] [c2 s2; -s2 c2]
+          A[p1 * LD + p2] = c2 * ra - s2 * rb;
+          A[p1 * LD + q2] = s2 * ra + c2 * rb;
+          A[q1 * LD + p2] = c2 * rc - s2 * rd;
+          A[q1 * LD + q2] = s2 * rc + c2 * rd;
+        } else {
+          const int u = t - NBLK;
+          const int k = u / J, row = u % J;
+          const S c = cs[k], sv = sn[k];
+          const int p = pp[k], q = qq[k];
+          const S vp = Vv[row * LD + p], vq = Vv[row * LD + q];
+          Vv[row * LD + p] = c * vp - sv * vq;
+          Vv[row * LD + q] = sv * vp + c * vq;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // descending order under a strict total order (value, then index)
+  if (tid < J) {
+    const double d = (double)A[tid * LD + tid];
+    th[tid] = isfinite(d) ? d : -DBL_MAX;
+  }
+  __syncthreads();
+  if (tid < J) {
+    int rank = 0;
+    const double x = th[tid];
+    for (int u = 0; u < J; ++u) {
+      const double y = th[u];
+      if (y > x || (y == x && u < tid)) ++rank;
+    }
+    order[rank] = tid;
+  }
+  __syncthreads();
+  for (int t = tid; t < J * J; t += blockDim.x) {
+    const int l = t / J, col = t % J;
+    Y[l * LD + col] = Vv[l * LD + order[col]];
+  }
+  __syncthreads();
+  // orthonormalise Y_keep (two passes of classical Gram-Schmidt per column)
+  for (int i = 0; i < keep; ++i) {
+    for (int pass = 0; pass < 2; ++pass) {
+      // h_l = y_l . y_i for l < i: warp w takes l = w, w + nw, ...
+      for (int l = warp; l < i; l += nw) {
+        S h = (S)0;
+        for (int r = lane; r < J; r += 32) h += Y[r * LD + l] * Y[r * LD + i];
+        for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
+        if (lane == 0) hbuf[l] = h;
+      }
+      __syncthreads();
+      if (tid < J) {
+        S v = Y[tid * LD + i];
+        for (int l = 0; l < i; ++l) v -= Y[tid * LD + l] * hbuf[l];
+        Y[tid * LD + i] = v;
+      }
+      __syncthreads();
+    }
+    if (warp == 0) {
+      S s2 = (S)0;
+      for (int r = lane; r < J; r += 32) s2 += Y[r * LD + i] * Y[r * LD + i];
+      for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+      if (lane == 0) nrm = (S)1 / sqrt(s2);
+    }
+    __syncthreads();
+    if (tid < J) Y[tid * LD + i] *= nrm;
+    __syncthreads();
+  }
+  // Z = T Y_keep; restarted projected matrix Y_keep^T T Y_keep
+  for (int t = tid; t < J * keep; t += blockDim.x) {
+    const int r = t / keep, i = t % keep;
+    S z = (S)0;
+    for (int c2 = 0; c2 < J; ++c2) z += Tc[r * LD + c2] * Y[c2 * LD + i];
+    Z[r * keep + i] = z;
+  }
+  __syncthreads();
+  for (int t = tid; t < JMAX * JMAX; t += blockDim.x) {
+    const int i = t / JMAX, j = t % JMAX;
+    double v = 0.0;
+    if (i < keep && j < keep) {
+      S acc = (S)0;
+      for (int r = 0; r < J; ++r) acc += Y[r * LD + i] * Z[r * keep + j];
+      v = (double)acc;
+    }
+    lz->T[t] = v;
+  }
+  for (int t = tid; t < J * J; t += blockDim.x) {
+    const int l = t / J, col = t % J;
+    lz->Y[l * JMAX + col] = (double)Y[l * LD + col];
+  }
+  if (tid < J) lz->theta[tid] = th[order[tid]];
+  __syncthreads();
+  // Ritz values of the orthonormalised vectors (Rayleigh quotients) and residual norms
+  // ||R_last E^T y_i|| for the top k_c
+  if (tid < kc) {
+    // residual of the Ritz pair (theta_i, Q y_i): Q (T y_i - theta_i y_i) + Q_res R E^T y_i,
+    // two orthogonal terms (y_i is only an approximate eigenvector of T)
+    const int i = tid;
+    S zz = (S)0;
+    for (int r = 0; r < J; ++r) zz += Y[r * LD + i] * Z[r * keep + i];
+    th[i] = (double)zz;
+    double s2 = 0.0;
+    for (int r = 0; r < J; ++r) {
+      const double e = (double)Z[r * keep + i] - (double)zz * (double)Y[r * LD + i];
+      s2 += e * e;
+    }
+    for (int a = 0; a < 8; ++a) {
+      double v = 0.0;
+      for (int c2 = a; c2 < 8; ++c2) v += lz->Rlast[a * 8 + c2] * (double)Y[(J - 8 + c2) * LD + i];
+      s2 += v * v;
+    }
+    lz->res[i] = sqrt(s2);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double scale = 0.0;
+    for (int i = 0; i < J; ++i) scale = fmax(scale, fabs((double)A[i * LD + i]));
+    lz->normest = fmax(lz->normest, scale);
+    int conv = 1;
+    for (int i = 0; i < kc; ++i) {
+      lz->theta[i] = th[i];
+      if (!(lz->res[i] <= tol * lz->normest)) conv = 0;
+    }
+    lz->converged = conv;
+    lz->cycles += 1;
+  }
+}
+
+// ---- App. B.2 interior point method --------------------------------------------------------
+struct IpmShared {
+  double Q[KSV * KSV];
+  double TS[KSV * KSV];
+  double L[KSV * (KSV + 1)];
+  double q12[KSV], h1[KSV], v[KSV], s[KSV], t[KSV], sinv[KSV], F1[KSV], ds[KSV], dt[KSV];
+  double fcol[KSV];
+  double S[64], T[64], Sinv[64], Lc[64], work[64], dS[64], dT[64], St[64], Tt[64];
+  double q22, h2, eta, zeta, omega, mu, deta, dzeta, domega, delta, kappa1, kappa2, det, r2, r3;
+  int map[KSV];
+  int piv, done, iters, has_eta;
+};
+
+__device__ __forceinline__ double aug_at(const double* aug, int r, int c) {
+  if (r > c) { int t = r; r = c; c = t; }
+  const int ti = r / 4, tj = c / 4;
+  int idx = 0;
+  for (int u = 0; u < ti; ++u) idx += 10 - u;
+  idx += tj - ti;
+  return aug[idx * 16 + (r % 4) * 4 + (c % 4)];
+}
+
+__device__ __forceinline__ void k_ipm_dev(DevScalars* sc, const double* USBS_RESTRICT red, int kc,
+                                             double alpha, double rho, double mu_tol, int max_iter,
+                                             int first_pass) {
+  __shared__ IpmShared sh;
+  const int tid = threadIdx.x;
+  const int K = kc * (kc + 1) / 2;
+  const double* aug = red + RED_AUG;
+  const double* vec = red + RED_VEC;
+  const double* vc = red + RED_VC;
+  if (tid == 0) {
+    int u = 0;
+    for (int q = 0; q < kc; ++q)
+      for (int p = q; p < kc; ++p) sh.map[u++] = svec_idx8(p, q);
+    sh.has_eta = sc->tr > 0.0 ? 1 : 0;
+    sc->has_eta = sh.has_eta;
+  }
+  __syncthreads();
+  const int has_eta = sh.has_eta;
+  const double tr = sc->tr, cx = sc->cx;
+  const double a2r = alpha * alpha / rho;
+  for (int t = tid; t < K * K; t += blockDim.x) {
+    const int i = t / K, j = t % K;
+    sh.Q[t] = a2r * aug_at(aug, sh.map[i], sh.map[j]);
+  }
+  if (tid < K) {
+    const int gi = sh.map[tid];
+    sh.q12[tid] = has_eta ? a2r / tr * aug_at(aug, gi, 36) : 0.0;
+    const double gtw = first_pass ? aug_at(aug, gi, 37) : vec[gi];
+    // svec of V^T C V (k_c x k_c block)
+    int p = 0, q = 0;
+    {
+      int u = tid;
+      for (q = 0; q < kc; ++q) {
+        if (u < kc - q) { p = q + u; break; }
+        u -= kc - q;
+      }
+    }
+    const double vcpq = 0.5 * (vc[p * 8 + q] + vc[q * 8 + p]);
+    const double svc = (p == q) ? vcpq : SQ2 * vcpq;
+    sh.h1[tid] = alpha * (gtw - svc);
+    sh.v[tid] = (p == q) ? 1.0 : 0.0;
+  }
+  if (tid == 0) {
+    sh.q22 = has_eta ? a2r / (tr * tr) * aug_at(aug, 36, 36) : 0.0;
+    const double axw = first_pass ? aug_at(aug, 36, 37) : vec[36];
+    sh.h2 = has_eta ? alpha * (axw - cx) / tr : 0.0;
+    // strictly feasible start (App. B.1 leaves it free)
+    for (int u = 0; u < 64; ++u) { sh.S[u] = 0.0; sh.T[u] = 0.0; }
+    for (int p = 0; p < kc; ++p) { sh.S[p * 8 + p] = 1.0 / (2.0 * kc); sh.T[p * 8 + p] = 1.0; }
+    sh.eta = has_eta ? 0.25 : 0.0;
+    sh.zeta = 1.0;
+    sh.omega = 1.0;
+    const double slack = 1.0 - 0.5 - sh.eta;
+    double m0 = kc * (1.0 / (2.0 * kc)) + sh.omega * slack;
+    if (has_eta) m0 += sh.eta * sh.zeta;
+    sh.mu = m0 / (has_eta ? 2.0 * (kc + 2) : 2.0 * (kc + 1));
+    sh.done = 0;
+    sh.iters = 0;
+  }
+  __syncthreads();
+  const int lane = tid & 31, warp = tid >> 5;
+  for (int it = 1; it <= max_iter; ++it) {
+    // S^-1 (warp-cooperative Cholesky and inverse)
+    if (warp == 0) {
+      warp_chol(sh.S, sh.Lc, kc);
+      warp_spd_inverse(sh.Lc, sh.work, sh.Sinv, kc);
+    }
+    __syncthreads();
+    if (tid < K) {
+      int p = 0, q = 0;
+      int u = tid;
+      for (q = 0; q < kc; ++q) {
+        if (u < kc - q) { p = q + u; break; }
+        u -= kc - q;
+      }
+      const double f = (p == q) ? 1.0 : SQ2;
+      sh.s[tid] = f * sh.S[p * 8 + q];
+      sh.t[tid] = f * sh.T[p * 8 + q];
+      sh.sinv[tid] = f * sh.Sinv[p * 8 + q];
+    }
+    // T (x)_s S^-1 entry by entry: (1/(s_a s_b)) (H_jk G_il + G_jk H_il + H_jl G_ik + G_jl H_ik)
+    // with G = T, H = S^-1, a = (i, j), b = (k, l), s = 2 on the diagonal and sqrt(2) off it
+    for (int t = tid; t < K * K; t += blockDim.x) {
+      const int ra = t / K, cb = t % K;
+      int i = 0, j = 0, k = 0, l = 0;
+      {
+        int u = ra;
+        for (j = 0; j < kc; ++j) { if (u < kc - j) { i = j + u; break; } u -= kc - j; }
+        u = cb;
+        for (l = 0; l < kc; ++l) { if (u < kc - l) { k = l + u; break; } u -= kc - l; }
+      }
+      const double inv_s = ((i == j) ? 0.5 : 1.0 / SQ2) * ((k == l) ? 0.5 : 1.0 / SQ2);
+      const double* G = sh.T;
+      const double* H = sh.Sinv;
+      sh.TS[t] = (H[j * 8 + k] * G[i * 8 + l] + G[j * 8 + k] * H[i * 8 + l] +
+                  H[j * 8 + l] * G[i * 8 + k] + G[j * 8 + l] * H[i * 8 + k]) * inv_s;
+    }
+    __syncthreads();
+    if (tid < K) {
+      double f1 = sh.h1[tid] - sh.t[tid] + sh.omega * sh.v[tid] + sh.eta * sh.q12[tid];
+      for (int c = 0; c < K; ++c) f1 += sh.Q[tid * K + c] * sh.s[c];
+      sh.F1[tid] = f1;
+    }
+    if (tid == 32) {
+      double trS = 0.0;
+      for (int p = 0; p < kc; ++p) trS += sh.S[p * 8 + p];
+      const double slack = 1.0 - trS - sh.eta;
+      sh.kappa1 = slack / sh.omega;
+      sh.r3 = sh.mu / sh.omega - slack;
+      if (has_eta) {
+        double qs = 0.0;
+        for (int c = 0; c < K; ++c) qs += sh.q12[c] * sh.s[c];
+        const double F2 = qs + sh.eta * sh.q22 + sh.h2 - sh.zeta + sh.omega;
+        sh.kappa2 = sh.zeta / sh.eta + sh.q22;
+        sh.r2 = -F2 + sh.mu / sh.eta - sh.zeta;
+        sh.det = sh.kappa1 * sh.kappa2 + 1.0;
+      }
+    }
+    __syncthreads();
+    // assemble [L | rhs] (eq. delta_S_linear_system2)
+    {
+      const double idet = has_eta ? 1.0 / sh.det : 0.0, ik1 = has_eta ? 0.0 : 1.0 / sh.kappa1;
+      for (int t = tid; t < K * (K + 1); t += blockDim.x) {
+        const int i = t / (K + 1), j = t % (K + 1);
+        double val;
+        if (j < K) {
+          val = sh.Q[i * K + j] + sh.TS[i * K + j];
+          if (has_eta)
+            val -= (sh.q12[i] * (sh.kappa1 * sh.q12[j] + sh.v[j]) +
+                    sh.v[i] * (sh.q12[j] - sh.kappa2 * sh.v[j])) * idet;
+          else
+            val += sh.v[i] * sh.v[j] * ik1;
+        } else {
+          val = -sh.F1[i] + sh.mu * sh.sinv[i] - sh.t[i];
+          if (has_eta)
+            val -= (sh.q12[i] * (sh.kappa1 * sh.r2 - sh.r3) + sh.v[i] * (sh.kappa2 * sh.r3 + sh.r2)) * idet;
+          else
+            val -= sh.v[i] * sh.r3 * ik1;
+        }
+        sh.L[t] = val;
+      }
+    }
+    __syncthreads();
+    // Gaussian elimination with partial pivoting
+    const int LDL = K + 1;
+    if (tid == 0) sh.piv = 0;
+    __syncthreads();
+    for (int p = 0; p < K; ++p) {
+      if (warp == 0) {
+        double best = -1.0;
+        int bi = p;
+        for (int r = p + lane; r < K; r += 32) {
+          const double x = fabs(sh.L[r * LDL + p]);
+          if (x > best) { best = x; bi = r; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          const double ob = __shfl_xor_sync(FULL, best, o);
+          const int oi = __shfl_xor_sync(FULL, bi, o);
+          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (bi != p)
+          for (int c = p + lane; c < LDL; c += 32) {
+            const double x = sh.L[p * LDL + c];
+            sh.L[p * LDL + c] = sh.L[bi * LDL + c];
+            sh.L[bi * LDL + c] = x;
+          }
+        __syncwarp();
+        if (lane == 0) {
+          // an exactly singular system (possible at degenerate optima): mark the
+          // direction unusable instead of dividing by zero
+          const double pv = sh.L[p * LDL + p];
+          sh.fcol[p] = (fabs(pv) > 1e-300) ? 1.0 / pv : 0.0;
+          if (!(fabs(pv) > 1e-300)) sh.piv = -1;
+        }
+      }
+      __syncthreads();
+      const double ipv = sh.fcol[p];
+      const int rows = K - p - 1, cols = LDL - p - 1;
+      for (int t = tid; t < rows * cols; t += blockDim.x) {
+        const int r = p + 1 + t / cols, c = p + 1 + t % cols;
+        sh.L[r * LDL + c] -= sh.L[r * LDL + p] * ipv * sh.L[p * LDL + c];
+      }
+      __syncthreads();
+    }
+    // back substitution (warp 0) with the reciprocal pivots kept in fcol
+    if (warp == 0) {
+      for (int r = K - 1; r >= 0; --r) {
+        double x = 0.0;
+        if (lane == 0) {
+          x = sh.L[r * LDL + K] * sh.fcol[r];
+          sh.ds[r] = x;
+        }
+        x = __shfl_sync(FULL, x, 0);
+        for (int i = lane; i < r; i += 32) sh.L[i * LDL + K] -= sh.L[i * LDL + r] * x;
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double vds = 0.0;
+      for (int c = 0; c < K; ++c) vds += sh.v[c] * sh.ds[c];
+      if (has_eta) {
+        double qds = 0.0;
+        for (int c = 0; c < K; ++c) qds += sh.q12[c] * sh.ds[c];
+        const double a = sh.r2 - qds, cc = sh.r3 + vds;
+        sh.deta = (sh.kappa1 * a - cc) / sh.det;
+        sh.domega = (sh.kappa2 * cc + a) / sh.det;
+        sh.dzeta = sh.mu / sh.eta - sh.zeta - (sh.zeta / sh.eta) * sh.deta;
+      } else {
+        sh.domega = (sh.r3 + vds) / sh.kappa1;
+        sh.deta = 0.0;
+        sh.dzeta = 0.0;
+      }
+    }
+    if (tid >= 32 && tid < 32 + K) {
+      const int r = tid - 32;
+      double x = sh.mu * sh.sinv[r] - sh.t[r];
+      for (int c = 0; c < K; ++c) x -= sh.TS[r * K + c] * sh.ds[c];
+      sh.dt[r] = x;
+    }
+    __syncthreads();
+    // a non-finite Newton direction (singular system): keep the current strictly
+    // feasible iterate and stop
+    if (tid == 0) {
+      bool fin = isfinite(sh.deta) && isfinite(sh.domega) && isfinite(sh.dzeta) && sh.piv >= 0;
+      for (int c = 0; c < K && fin; ++c) fin = isfinite(sh.ds[c]) && isfinite(sh.dt[c]);
+      sh.done = fin ? 0 : 2;
+    }
+    __syncthreads();
+    if (sh.done == 2) break;
+    if (tid < 64) {
+      // smat of ds, dt
+      const int p = tid / 8, q = tid % 8;
+      double vs = 0.0, vt = 0.0;
+      if (p < kc && q < kc) {
+        const int pi = max(p, q), qi = min(p, q);
+        const int u = svec_idx(pi, qi, kc);
+        const double f = (p == q) ? 1.0 : 1.0 / SQ2;
+        vs = f * sh.ds[u];
+        vt = f * sh.dt[u];
+      }
+      sh.dS[tid] = vs;
+      sh.dT[tid] = vt;
+    }
+    if (tid == 0) sh.delta = 1.0;
+    __syncthreads();
+    // backtracking: halve until strictly feasible (warps 0 and 1 test S and T), then 0.95 delta
+    for (int ls = 0; ls < 80; ++ls) {
+      const double delta = sh.delta;
+      if (tid < 64) {
+        const int p = tid / 8, q = tid % 8;
+        sh.St[tid] = sh.S[tid] + delta * sh.dS[tid];
+        sh.Tt[tid] = sh.T[tid] + delta * sh.dT[tid];
+        (void)p; (void)q;
+      }
+      __syncthreads();
+      bool okw = true;
+      if (warp == 0) okw = warp_chol(sh.St, nullptr, kc);
+      if (warp == 1) okw = warp_chol(sh.Tt, nullptr, kc);
+      if (lane == 0 && warp < 2) sh.fcol[warp] = okw ? 1.0 : 0.0;
+      __syncthreads();
+      if (tid == 0) {
+        double trS = 0.0;
+        for (int p = 0; p < kc; ++p) trS += sh.St[p * 8 + p];
+        const double en = sh.eta + delta * sh.deta, zn = sh.zeta + delta * sh.dzeta;
+        const double on = sh.omega + delta * sh.domega;
+        bool ok = on > 0.0 && (1.0 - trS - en) > 0.0 && sh.fcol[0] > 0.5 && sh.fcol[1] > 0.5;
+        if (has_eta) ok = ok && en > 0.0 && zn > 0.0;
+        sh.done = ok ? 1 : 0;
+        if (!ok) sh.delta = 0.5 * delta;
+      }
+      __syncthreads();
+      if (sh.done) break;
+    }
+    __syncthreads();
+    const double delta = 0.95 * sh.delta;
+    if (tid < 64) {
+      const int p = tid / 8, q = tid % 8;
+      double sv = sh.S[tid], tv = sh.T[tid];
+      if (p < kc && q < kc) {
+        sv = sh.S[tid] + 0.5 * delta * (sh.dS[p * 8 + q] + sh.dS[q * 8 + p]);
+        tv = sh.T[tid] + 0.5 * delta * (sh.dT[p * 8 + q] + sh.dT[q * 8 + p]);
+      }
+      sh.St[tid] = sv;
+      sh.Tt[tid] = tv;
+    }
+    __syncthreads();
+    if (tid < 64) {
+      sh.S[tid] = sh.St[tid];
+      sh.T[tid] = sh.Tt[tid];
+    }
+    __syncthreads();
+    if (tid == 0) {
+      sh.omega += delta * sh.domega;
+      if (has_eta) {
+        sh.eta += delta * sh.deta;
+        sh.zeta += delta * sh.dzeta;
+      }
+      double st = 0.0, trS = 0.0;
+      for (int p = 0; p < kc; ++p)
+        for (int q = 0; q < kc; ++q) st += sh.S[p * 8 + q] * sh.T[p * 8 + q];
+      for (int p = 0; p < kc; ++p) trS += sh.S[p * 8 + p];
+      double mest = st + sh.omega * (1.0 - trS - sh.eta);
+      if (has_eta) mest += sh.eta * sh.zeta;
+      mest /= has_eta ? 2.0 * (kc + 2) : 2.0 * (kc + 1);
+      const double gamma = sh.delta * 0.95 <= 0.2 ? 1.0 : 0.5 - 0.4 * delta * delta;
+      sh.mu = fmin(sh.mu, gamma * mest);
+      sh.iters = it;
+      sh.done = (sh.mu < mu_tol || !isfinite(sh.mu)) ? 1 : 0;
+    }
+    __syncthreads();
+    if (sh.done) break;
+  }
+  if (tid == 0) {
+    for (int u = 0; u < 64; ++u) {
+      sc->S_hat[u] = sh.S[u];
+      sc->S[u] = alpha * sh.S[u];
+    }
+    sc->eta_hat = sh.eta;
+    sc->eta = has_eta ? alpha * sh.eta / tr : 0.0;
+    sc->theta_ipm[0] = sh.zeta;
+    sc->theta_ipm[1] = sh.omega;
+    sc->theta_ipm[2] = sh.mu;
+    sc->ipm_iters += sh.iters;
+    if (!isfinite(sh.mu) || !isfinite(sh.eta)) sc->status = USBS_ENUMERIC;
+  }
+}
+
+// ---- model value, descent test, implicit primal update and gates ------------------------------
+// red + RED_VEC holds the reduced candidate sums of k_xupdate:
+// [0,36) G^T y~, 36 <b, y~>, 37 <A Xbar, y~>, 38 sum d^2, 39 max |d|.
+__device__ __forceinline__ void k_finish_dev(DevScalars* sc, const DevLanczos* lz, const double* USBS_RESTRICT red, int kc,
+                         double alpha, double beta, double bnorm) {
+  __shared__ double Zs[64];
+  __shared__ float Af[64], Vf[64];
+  const double* vec = red + RED_VEC;
+  const double* vc = red + RED_VC;
+  // V^T (C - A*(y~)) V = V^T C V - smat(G^T y~)
+  for (int t = threadIdx.x; t < 64; t += 32) {
+    const int p = t / 8, q = t % 8;
+    double z = 0.0;
+    if (p < kc && q < kc) {
+      const int pi = max(p, q), qi = min(p, q);
+      const double g = vec[svec_idx8(pi, qi)];
+      z = 0.5 * (vc[p * 8 + q] + vc[q * 8 + p]) - ((p == q) ? g : g / SQ2);
+    }
+    Zs[t] = z;
+  }
+  __syncwarp();
+  const double lamV = warp_lambda_max(Zs, kc, Af, Vf);
+  if (threadIdx.x != 0) return;
+  double Vc[64];
+  for (int p = 0; p < 8; ++p)
+    for (int q = 0; q < 8; ++q) Vc[p * 8 + q] = 0.5 * (vc[p * 8 + q] + vc[q * 8 + p]);
+  double cxS = 0.0, trS = 0.0;
+  for (int p = 0; p < kc; ++p) {
+    trS += sc->S[p * 8 + p];
+    for (int q = 0; q < kc; ++q) cxS += Vc[p * 8 + q] * sc->S[p * 8 + q];
+  }
+  const double cx_new = sc->eta * sc->cx + cxS;
+  const double tr_new = sc->eta * sc->tr + trS;
+  const double bty = vec[36], axy = vec[37];
+  double best = fmax(0.0, lamV);
+  if (sc->has_eta) best = fmax(best, (sc->cx - axy) / sc->tr);
+  const double f_hat = bty + alpha * best;
+  const double lam = lz->theta[0];
+  const double f_cand = alpha * fmax(lam, 0.0) + bty;
+  const double f_old = sc->f_y;
+  const int descent = (beta * (f_old - f_hat) <= f_old - f_cand) ? 1 : 0;
+  sc->descent = descent;
+  if (descent) sc->f_y = f_cand;
+  sc->f_hat = f_hat;
+  sc->f_cand = f_cand;
+  sc->lam_max = lam;
+  sc->bty = bty;
+  sc->axy = axy;
+  sc->cx_new = cx_new;
+  sc->tr_new = tr_new;
+  sc->cx = cx_new;
+  sc->tr = tr_new;
+  sc->relgap = fabs(sc->f_y - cx_new) / (1.0 + fabs(cx_new));
+  sc->relinf = sqrt(fmax(vec[38], 0.0)) / (1.0 + bnorm);
+  sc->relinf_max = vec[39];
+  sc->t += 1;
+  if (!isfinite(sc->f_y) || !isfinite(cx_new)) sc->status = USBS_ENUMERIC;
+}
+
+__device__ __forceinline__ void k_cold_dev(DevScalars* sc, const DevLanczos* lz, double alpha) {
+  if (threadIdx.x != 0) return;
+  sc->f_y = alpha * fmax(lz->theta[0], 0.0);
+  sc->cx = 0.0;
+  sc->tr = 0.0;
+  sc->has_eta = 0;
+  sc->t = 0;
+  sc->status = 0;
+  sc->lam_max = lz->theta[0];
+}
+
+__device__ __forceinline__ void k_begin_step_dev(DevScalars* sc) {
+  if (threadIdx.x != 0) return;
+  sc->ipm_iters = 0;
+  sc->n_alt = 0;
+}
+
+__device__ __forceinline__ void k_commit_dev(const int cta, const int ncta, int m, const DevScalars* USBS_RESTRICT sc, const double* USBS_RESTRICT ycand,
+                         double* USBS_RESTRICT y) {
+  if (!sc->descent) return;
+  for (int c = cta * blockDim.x + threadIdx.x; c < m; c += ncta * blockDim.x) y[c] = ycand[c];
+}
+
+__device__ __forceinline__ void k_lanczos_reset_dev(DevLanczos* lz) {
+  for (int t = threadIdx.x; t < JMAX * JMAX; t += blockDim.x) lz->T[t] = 0.0;
+  if (threadIdx.x == 0) {
+    lz->sweeps = 0;
+    lz->status = 0;
+    lz->defl = 0;
+    lz->converged = 0;
+    lz->cycles = 0;
+    lz->normest = 0.0;
+  }
+}
+
+}  // namespace
+}  // namespace usbs

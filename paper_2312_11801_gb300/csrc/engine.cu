@@ -634,8 +634,8 @@ static int step_impl(Ctx* c, usbs_step_info* info) {
   const int npg = red_grid(c, c->m, 128);
   // V^T C V
   Bulk<T>::spmm(c, c->valC, c->dC, c->V, c->W);
-  Bulk<T>::gram_xy(c, c->V, c->W, np);
-  reduce_partials(c, np, 64, c->red + RED_VC);
+  Orth<T>::gram_xy(c, c->V, c->W);
+  reduce_partials(c, orth_grid(c, c->n), 64, c->red + RED_VC);
   // [G | A Xbar | y - b/rho]^T [G | A Xbar | y - b/rho]
   Bulk<T>::gstats(c, c->V, c->ax, c->y, npg);
   reduce_partials(c, npg, 880, c->red + RED_AUG);
@@ -828,6 +828,34 @@ int usbs_solve(usbs_ctx* ctx, int warm_start, double tol, usbs_result* out) {
   if (rc != USBS_OK) return rc;
   return res.converged ? USBS_OK : USBS_ENOTCONV;
 }
+
+}  // extern "C"
+
+namespace usbs {
+int batch_result(Ctx* c, usbs_result* out) {
+  USBS_CUDA_TRY(c, cudaMemcpyAsync(c->h_sc, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost,
+                                   c->stream));
+  USBS_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  usbs_result res;
+  std::memset(&res, 0, sizeof(res));
+  res.iters = c->batch_iters;
+  res.converged = c->batch_converged;
+  res.descent_steps = c->batch_descent;
+  res.matvecs = c->batch_matvecs;
+  if (c->batch_iters > 0) {
+    c->h_sc->n_alt = c->batch_n_alt;
+    fill_info(c, *c->h_sc, c->batch_last_matvecs, &res.last);
+  }
+  if (out) *out = res;
+  if (c->batch_status != USBS_OK) {
+    c->err = "non-finite value in the batched solve";
+    return c->batch_status;
+  }
+  return res.converged ? USBS_OK : USBS_ENOTCONV;
+}
+}  // namespace usbs
+
+extern "C" {
 
 int usbs_get_sketch(usbs_ctx* ctx, float* P, float* Psi, double* scalars) {
   if (!ctx) return USBS_EINVAL;

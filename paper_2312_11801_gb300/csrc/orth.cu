@@ -14,213 +14,24 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "dev_orth.cuh"
 
 namespace usbs {
 namespace {
-
-template <typename T> struct TileRows;
-template <> struct TileRows<float> { static constexpr int value = 128; };
-template <> struct TileRows<double> { static constexpr int value = 64; };
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
-  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  const int src_bytes = valid ? 16 : 0;   // 0: fill the 16 bytes with zeros
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::); }
-__device__ __forceinline__ void cp_async_wait_0() { asm volatile("cp.async.wait_group 0;\n" ::); }
-
-// Copy rows [row0, row0 + TR) of blocks 0..nq-1 of Q (and of W if W != nullptr, placed
-// after them) into one stage: layout stage[blk][r][8].
-template <typename T, int TR>
-__device__ __forceinline__ void load_tile(T* stage, const T* __restrict__ Q, size_t bstride, int nq,
-                                          const T* __restrict__ W, int n, int row0) {
-  constexpr int CH = 8 * sizeof(T) / 16;           // 16-byte chunks per row
-  const int nblk = nq + (W ? 1 : 0);
-  const int total = nblk * TR * CH;
-  for (int u = threadIdx.x; u < total; u += blockDim.x) {
-    const int b = u / (TR * CH);
-    const int rem = u % (TR * CH);
-    const int r = rem / CH, ch = rem % CH;
-    const int row = row0 + r;
-    const bool valid = row < n;
-    const T* src = (b < nq ? Q + b * bstride : W) + (size_t)8 * (valid ? row : 0) + ch * (16 / sizeof(T));
-    cp_async16(stage + ((size_t)b * TR + r) * 8 + ch * (16 / sizeof(T)), src, valid);
-  }
-}
-
-// ---- H = Q^T W --------------------------------------------------------------------------
-// Items (b, a-pair): 4 nb <= 32.  256 threads = 8 row groups x 32 slots; a slot owns one
-// item: 2 basis columns x all 8 columns of W (16 accumulators, 3 shared loads per 16 FMAs).
-template <typename T>
-__device__ __forceinline__ void accum_pair(const T* __restrict__ qcol2, const T* __restrict__ X,
-                                           int grp, T (&acc)[16]) {
-  constexpr int TR = TileRows<T>::value;
-  for (int r = grp; r < TR; r += 8) {
-    const T q0 = qcol2[r * 8], q1 = qcol2[r * 8 + 1];
-    const T* xr = X + r * 8;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      acc[c] += q0 * xr[c];
-      acc[8 + c] += q1 * xr[c];
-    }
-  }
-}
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_tproj(int n, const T* __restrict__ Q, size_t bstride, int nb,
                                                const T* __restrict__ W, double* __restrict__ partials,
                                                const int* __restrict__ mask) {
-  if (mask && *mask == 0) return;
-  constexpr int TR = TileRows<T>::value;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* stages = reinterpret_cast<T*>(smem_raw);
-  const int sstride = (nb + 1) * TR * 8;
-  const int tid = threadIdx.x, grp = tid >> 5, slot = tid & 31;
-  const int nitems = 4 * nb;
-  T acc[16];
-#pragma unroll
-  for (int u = 0; u < 16; ++u) acc[u] = (T)0;
-  const int ntiles = (n + TR - 1) / TR;
-  int tile = blockIdx.x;
-  if (tile < ntiles) load_tile<T, TR>(stages, Q, bstride, nb, W, n, tile * TR);
-  cp_async_commit();
-  for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
-    const int next = tile + gridDim.x;
-    if (next < ntiles) load_tile<T, TR>(stages + ((it + 1) & 1) * sstride, Q, bstride, nb, W, n, next * TR);
-    cp_async_commit();
-    cp_async_wait_1();
-    __syncthreads();
-    const T* st = stages + (it & 1) * sstride;
-    if (slot < nitems) {
-      const int b = slot >> 2, a0 = 2 * (slot & 3);
-      accum_pair<T>(st + (size_t)b * TR * 8 + a0, st + nb * TR * 8, grp, acc);
-    }
-    __syncthreads();
-  }
-  cp_async_wait_0();
-  __syncthreads();
-  double* red = reinterpret_cast<double*>(smem_raw);     // 8 x 512
-  if (slot < nitems) {
-    const int b = slot >> 2, a0 = 2 * (slot & 3);
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      red[grp * 512 + b * 64 + a0 * 8 + c] = (double)acc[c];
-      red[grp * 512 + b * 64 + (a0 + 1) * 8 + c] = (double)acc[8 + c];
-    }
-  }
-  __syncthreads();
-  for (int t = tid; t < nb * 64; t += blockDim.x) {
-    double sum = 0.0;
-#pragma unroll
-    for (int g = 0; g < 8; ++g) sum += red[g * 512 + t];
-    partials[(size_t)blockIdx.x * PART_STRIDE + t] = sum;
-  }
+  k_tproj_dev<T>(blockIdx.x, gridDim.x, n, Q, bstride, nb, W, partials, mask);
 }
 
-// ---- X = W - Q H; H2 = Q^T X; G = X^T X -----------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256) k_tupdate(int n, const T* __restrict__ Q, size_t bstride, int nb,
                                                  T* __restrict__ W, const double* __restrict__ Hred,
                                                  double* __restrict__ partials,
                                                  const int* __restrict__ mask) {
-  if (mask && *mask == 0) return;
-  constexpr int TR = TileRows<T>::value;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* stages = reinterpret_cast<T*>(smem_raw);
-  const int sstride = (nb + 1) * TR * 8;
-  T* Hs = stages + 2 * sstride;                             // nb x 8 x 8
-  const int tid = threadIdx.x, grp = tid >> 5, slot = tid & 31;
-  for (int t = tid; t < nb * 64; t += blockDim.x) Hs[t] = (T)Hred[t];
-  const int nitems = 4 * (nb + 1);                          // item b == nb: the Gram matrix
-  T acc[2][16];
-#pragma unroll
-  for (int u = 0; u < 2; ++u)
-#pragma unroll
-    for (int v = 0; v < 16; ++v) acc[u][v] = (T)0;
-  const int ntiles = (n + TR - 1) / TR;
-  int tile = blockIdx.x;
-  if (tile < ntiles) load_tile<T, TR>(stages, Q, bstride, nb, W, n, tile * TR);
-  cp_async_commit();
-  // phase-1 mapping: row r = tid / 2 (2 passes when TR = 128 needs 2 rows per thread pair)
-  for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
-    const int next = tile + gridDim.x;
-    if (next < ntiles) load_tile<T, TR>(stages + ((it + 1) & 1) * sstride, Q, bstride, nb, W, n, next * TR);
-    cp_async_commit();
-    cp_async_wait_1();
-    __syncthreads();
-    T* st = stages + (it & 1) * sstride;
-    T* Xs = st + nb * TR * 8;                               // W tile, overwritten by X
-    // phase 1: X = W - Q H, 4 columns per thread
-    for (int p = tid; p < TR * 2; p += blockDim.x) {
-      const int r = p >> 1, c0 = 4 * (p & 1);
-      T x[4];
-#pragma unroll
-      for (int v = 0; v < 4; ++v) x[v] = Xs[r * 8 + c0 + v];
-      for (int b = 0; b < nb; ++b) {
-        const T* qr = st + ((size_t)b * TR + r) * 8;
-        const T* hb = Hs + b * 64 + c0;
-#pragma unroll
-        for (int ap = 0; ap < 8; ++ap) {
-          const T q = qr[ap];
-#pragma unroll
-          for (int v = 0; v < 4; ++v) x[v] -= q * hb[ap * 8 + v];
-        }
-      }
-#pragma unroll
-      for (int v = 0; v < 4; ++v) Xs[r * 8 + c0 + v] = x[v];
-      const int row = tile * TR + r;
-      if (row < n) {
-#pragma unroll
-        for (int v = 0; v < 4; ++v) W[(size_t)8 * row + c0 + v] = x[v];
-      }
-    }
-    __syncthreads();
-    // phase 2: H2 += Q^T X and G += X^T X (rows past n are zero in X)
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int item = slot + 32 * u;
-      if (item < nitems) {
-        const int b = item >> 2, a0 = 2 * (item & 3);
-        accum_pair<T>((b < nb ? st + (size_t)b * TR * 8 : Xs) + a0, Xs, grp, acc[u]);
-      }
-    }
-    __syncthreads();
-  }
-  cp_async_wait_0();
-  __syncthreads();
-  double* red = reinterpret_cast<double*>(smem_raw);     // 8 x 576
-#pragma unroll
-  for (int u = 0; u < 2; ++u) {
-    const int item = slot + 32 * u;
-    if (item < nitems) {
-      const int b = item >> 2, a0 = 2 * (item & 3);
-      const int base = (b < nb ? b * 64 : 512) + a0 * 8;
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        red[grp * 576 + base + c] = (double)acc[u][c];
-        red[grp * 576 + base + 8 + c] = (double)acc[u][8 + c];
-      }
-    }
-  }
-  __syncthreads();
-  for (int t = tid; t < 576; t += blockDim.x) {
-    if (t < 512 && t >= nb * 64) continue;
-    double sum = 0.0;
-#pragma unroll
-    for (int g = 0; g < 8; ++g) sum += red[g * 576 + t];
-    partials[(size_t)blockIdx.x * PART_STRIDE + t] = sum;
-  }
-}
-
-// ---- out = (W - Q H2) R^-1; deficient columns replaced by random vectors -----------------------
-__device__ __forceinline__ double hash_uniform_o(uint64_t seed, uint64_t row, uint64_t col) {
-  uint64_t z = seed + 0x9E3779B97F4A7C15ull * (row * 16 + col + 1);
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  z = z ^ (z >> 31);
-  return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+  k_tupdate_dev<T>(blockIdx.x, gridDim.x, n, Q, bstride, nb, W, Hred, partials, mask);
 }
 
 template <typename T>
@@ -228,137 +39,15 @@ __global__ void __launch_bounds__(256) k_tfinalize(int n, const T* __restrict__ 
                                                    int nb, const T* W, const double* __restrict__ H2red,
                                                    const DevLanczos* __restrict__ lz, T* out,
                                                    const int* __restrict__ mask, uint64_t seed) {
-  if (mask && *mask == 0) return;
-  constexpr int TR = TileRows<T>::value;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* stages = reinterpret_cast<T*>(smem_raw);
-  const int sstride = (nb + 1) * TR * 8;
-  T* Hs = stages + 2 * sstride;
-  T* Ri = Hs + 8 * 64;
-  __shared__ int dfc[8];
-  const int tid = threadIdx.x;
-  for (int t = tid; t < nb * 64; t += blockDim.x) Hs[t] = (T)H2red[t];
-  if (tid < 64) Ri[tid] = (T)lz->Rinv[tid];
-  if (tid < 8) dfc[tid] = lz->dcol[tid];
-  const int ntiles = (n + TR - 1) / TR;
-  int tile = blockIdx.x;
-  if (tile < ntiles) load_tile<T, TR>(stages, Q, bstride, nb, W, n, tile * TR);
-  cp_async_commit();
-  for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
-    const int next = tile + gridDim.x;
-    if (next < ntiles) load_tile<T, TR>(stages + ((it + 1) & 1) * sstride, Q, bstride, nb, W, n, next * TR);
-    cp_async_commit();
-    cp_async_wait_1();
-    __syncthreads();
-    T* st = stages + (it & 1) * sstride;
-    T* Xs = st + nb * TR * 8;
-    for (int p = tid; p < TR * 2; p += blockDim.x) {
-      const int r = p >> 1, c0 = 4 * (p & 1);
-      T x[4];
-#pragma unroll
-      for (int v = 0; v < 4; ++v) x[v] = Xs[r * 8 + c0 + v];
-      for (int b = 0; b < nb; ++b) {
-        const T* qr = st + ((size_t)b * TR + r) * 8;
-        const T* hb = Hs + b * 64 + c0;
-#pragma unroll
-        for (int ap = 0; ap < 8; ++ap) {
-          const T q = qr[ap];
-#pragma unroll
-          for (int v = 0; v < 4; ++v) x[v] -= q * hb[ap * 8 + v];
-        }
-      }
-      __syncwarp();
-#pragma unroll
-      for (int v = 0; v < 4; ++v) Xs[r * 8 + c0 + v] = x[v];
-    }
-    __syncthreads();
-    for (int p = tid; p < TR * 2; p += blockDim.x) {
-      const int r = p >> 1, c0 = 4 * (p & 1);
-      const int row = tile * TR + r;
-      if (row >= n) continue;
-      const T* xr = Xs + r * 8;
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        const int a = c0 + v;
-        T o = (T)0;
-#pragma unroll
-        for (int c = 0; c < 8; ++c) o += xr[c] * Ri[c * 8 + a];
-        if (dfc[a] == 1) o = (T)hash_uniform_o(seed, (uint64_t)row, (uint64_t)a);
-        else if (dfc[a] == 2) o = (T)0;
-        out[(size_t)8 * row + a] = o;
-      }
-    }
-    __syncthreads();
-  }
-  cp_async_wait_0();
+  k_tfinalize_dev<T>(blockIdx.x, gridDim.x, n, Q, bstride, nb, W, H2red, lz, out, mask, seed);
 }
 
-
-// ---- out[o] = Q[:, :J] Y[:, 8o : 8o + 8], o < nout (thick restart, Ritz vectors) -------------
-// Optionally copies the residual block into out[resid_slot].  Y (J x 8 nout) sits in shared
-// memory; a thread owns (row, 4 output columns) items.
 template <typename T>
 __global__ void __launch_bounds__(256) k_trestart(int n, const T* __restrict__ Q, size_t bstride, int nbk,
                                                   int nout, const double* __restrict__ Y,
                                                   T* __restrict__ out, size_t ostride,
                                                   const T* __restrict__ resid, int resid_slot) {
-  constexpr int TR = TileRows<T>::value;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* stages = reinterpret_cast<T*>(smem_raw);
-  const int sstride = nbk * TR * 8;
-  T* Ys = stages + 2 * sstride;                       // J x ncol
-  const int J = nbk * 8, ncol = nout * 8;
-  const int tid = threadIdx.x;
-  for (int t = tid; t < J * ncol; t += blockDim.x) Ys[t] = (T)Y[(t / ncol) * JMAX + (t % ncol)];
-  const int ntiles = (n + TR - 1) / TR;
-  int tile = blockIdx.x;
-  if (tile < ntiles) load_tile<T, TR>(stages, Q, bstride, nbk, nullptr, n, tile * TR);
-  cp_async_commit();
-  for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
-    const int next = tile + gridDim.x;
-    if (next < ntiles) load_tile<T, TR>(stages + ((it + 1) & 1) * sstride, Q, bstride, nbk, nullptr, n, next * TR);
-    cp_async_commit();
-    cp_async_wait_1();
-    __syncthreads();
-    const T* st = stages + (it & 1) * sstride;
-    for (int p = tid; p < (TR / 2) * nout; p += blockDim.x) {
-      const int r0 = 2 * (p / nout), o = p % nout;
-      T acc0[8], acc1[8];
-#pragma unroll
-      for (int v = 0; v < 8; ++v) { acc0[v] = (T)0; acc1[v] = (T)0; }
-      for (int b = 0; b < nbk; ++b) {
-        const T* qr0 = st + ((size_t)b * TR + r0) * 8;
-        const T* qr1 = qr0 + 8;
-#pragma unroll
-        for (int a = 0; a < 8; ++a) {
-          const T q0 = qr0[a], q1 = qr1[a];
-          const T* yr = Ys + (b * 8 + a) * ncol + 8 * o;
-#pragma unroll
-          for (int v = 0; v < 8; ++v) {
-            acc0[v] += q0 * yr[v];
-            acc1[v] += q1 * yr[v];
-          }
-        }
-      }
-      const int row0 = tile * TR + r0;
-      if (row0 < n) {
-#pragma unroll
-        for (int v = 0; v < 8; ++v) out[o * ostride + (size_t)8 * row0 + v] = acc0[v];
-      }
-      if (row0 + 1 < n) {
-#pragma unroll
-        for (int v = 0; v < 8; ++v) out[o * ostride + (size_t)8 * (row0 + 1) + v] = acc1[v];
-      }
-    }
-    if (resid) {
-      for (int p = tid; p < TR * 8; p += blockDim.x) {
-        const int row = tile * TR + p / 8;
-        if (row < n) out[resid_slot * ostride + (size_t)8 * row + (p % 8)] = resid[(size_t)8 * row + (p % 8)];
-      }
-    }
-    __syncthreads();
-  }
-  cp_async_wait_0();
+  k_trestart_dev<T>(blockIdx.x, gridDim.x, n, Q, bstride, nbk, nout, Y, out, ostride, resid, resid_slot);
 }
 
 template <typename T>
@@ -397,6 +86,15 @@ void Orth<T>::proj(Ctx* c, const void* Qb, int nb, const void* W, const int* mas
   const size_t sm = std::max(tile_smem<T>(nb, 0), sizeof(double) * 8 * 512);
   k_tproj<T><<<orth_grid(c, c->n), 256, sm, c->stream>>>((int)c->n, (const T*)Qb, (size_t)c->n * 8,
                                                          nb, (const T*)W, c->partials, mask);
+}
+
+template <typename T>
+void Orth<T>::gram_xy(Ctx* c, const void* X, const void* Y) {
+  USBS_LAUNCH_B(c, USBS_KIND_REORTH, 16.0 * sizeof(T) * c->n);
+  set_attrs<T>();
+  const size_t sm = std::max(tile_smem<T>(1, 0), sizeof(double) * 8 * 512);
+  k_tproj<T><<<orth_grid(c, c->n), 256, sm, c->stream>>>((int)c->n, (const T*)X, (size_t)c->n * 8,
+                                                         1, (const T*)Y, c->partials, nullptr);
 }
 
 template <typename T>

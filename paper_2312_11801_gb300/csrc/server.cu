@@ -386,22 +386,61 @@ int usbs_batch_solve(usbs_ctx** ctxs, int count, double tol, int max_concurrency
                      usbs_result* results, int* status) {
   if (!ctxs || count < 0 || !results || !(tol > 0.0)) return USBS_EINVAL;
   if (count == 0) return USBS_OK;
-  const int nt = std::max(1, std::min(count, max_concurrency > 0 ? max_concurrency : 8));
+  for (int i = 0; i < count; ++i)
+    if (!ctxs[i]) return USBS_EINVAL;
+  // contexts the persistent kernel can take, grouped by (precision, basis); one launch
+  // per group solves all of its instances
+  std::vector<std::vector<usbs::Ctx*>> groups;
+  std::vector<std::vector<int>> group_idx;
+  std::vector<int> rest;
+  for (int i = 0; i < count; ++i) {
+    usbs::Ctx* c = reinterpret_cast<usbs::Ctx*>(ctxs[i]);
+    if (!usbs::batch_eligible(c)) { rest.push_back(i); continue; }
+    size_t g = 0;
+    for (; g < groups.size(); ++g)
+      if (groups[g][0]->fp64 == c->fp64 && groups[g][0]->J == c->J) break;
+    if (g == groups.size()) { groups.emplace_back(); group_idx.emplace_back(); }
+    groups[g].push_back(c);
+    group_idx[g].push_back(i);
+  }
+  int worst = USBS_OK;
+  for (size_t g = 0; g < groups.size(); ++g) {
+    for (usbs::Ctx* c : groups[g])
+      if (cudaStreamSynchronize(c->stream) != cudaSuccess) return USBS_ECUDA;
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return USBS_ECUDA;
+    std::string err;
+    const int rc = usbs::batch_run(groups[g], st, tol, err);
+    cudaStreamDestroy(st);
+    if (rc != USBS_OK) {
+      for (usbs::Ctx* c : groups[g]) c->err = err;
+      return rc;
+    }
+    for (size_t k = 0; k < groups[g].size(); ++k) {
+      const int i = group_idx[g][k];
+      const int r = usbs::batch_result(groups[g][k], &results[i]);
+      if (status) status[i] = r;
+      if (r != USBS_OK && r != USBS_ENOTCONV) worst = r;
+    }
+  }
+  if (rest.empty()) return worst;
+  const int nt = std::max(1, std::min((int)rest.size(), max_concurrency > 0 ? max_concurrency : 8));
   std::atomic<int> next{0};
-  std::atomic<int> worst{USBS_OK};
+  std::atomic<int> worst_t{USBS_OK};
   std::vector<std::thread> th;
   for (int t = 0; t < nt; ++t)
     th.emplace_back([&] {
       for (;;) {
-        const int i = next.fetch_add(1);
-        if (i >= count) break;
+        const int k = next.fetch_add(1);
+        if (k >= (int)rest.size()) break;
+        const int i = rest[k];
         const int rc = usbs_solve(ctxs[i], 0, tol, &results[i]);
         if (status) status[i] = rc;
-        if (rc != USBS_OK && rc != USBS_ENOTCONV) worst.store(rc);
+        if (rc != USBS_OK && rc != USBS_ENOTCONV) worst_t.store(rc);
       }
     });
   for (auto& t : th) t.join();
-  return worst.load();
+  return worst != USBS_OK ? worst : worst_t.load();
 }
 
 }  // extern "C"

@@ -1,0 +1,107 @@
+"""The persistent batched solver (one CTA per instance, whole solve in one launch).
+
+It runs the same steps as usbs_solve from the same device bodies, so its results must
+agree with the per-step path within the solve tolerance; since one CTA works through an
+instance in a fixed order, a solve must come out bit for bit the same alone and inside
+a mixed batch.
+"""
+import numpy as np
+import pytest
+
+from paper_2312_11801_gb300 import instances as I
+from tests.gpu_util import gpu_modules
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-3
+CAP = 800
+
+
+@pytest.fixture(scope="module")
+def mods():
+    return gpu_modules()
+
+
+def _mix():
+    probs = [I.maxcut_torus(s, seed=s, signed=True) for s in (10, 12, 16)]
+    probs += [I.maxcut_er(n, 8.0, seed=n, weights="uniform") for n in (100, 180, 260)]
+    return probs
+
+
+def _batch(U, probs, **kw):
+    ctxs = [U.usbs_create(p, max_iters=CAP, **kw) for p in probs]
+    try:
+        res, st = U.usbs_batch_solve(ctxs, tol=TOL, max_concurrency=4)
+        duals = [U.usbs_get_dual(c) for c in ctxs]
+    finally:
+        for c in ctxs:
+            c.close()
+    return res, st, duals
+
+
+@pytest.mark.parametrize("basis", [32, 64])
+def test_alone_and_in_the_mix_are_identical(mods, basis):
+    torch, U = mods
+    probs = _mix()
+    mix, st, ymix = _batch(U, probs, lanczos_basis=basis)
+    for i in (0, 4):
+        alone, st1, y1 = _batch(U, [probs[i]], lanczos_basis=basis)
+        a, b = alone[0], mix[i]
+        assert a["iters"] == b["iters"] and a["converged"] == b["converged"]
+        assert a["last"]["objective"] == b["last"]["objective"]
+        assert a["last"]["dual_bound"] == b["last"]["dual_bound"]
+        assert np.array_equal(y1[0], ymix[i])
+
+
+@pytest.mark.parametrize("precision,basis", [(1, 32), (1, 64), (0, 32)])
+def test_batched_agrees_with_per_step_path(mods, precision, basis):
+    torch, U = mods
+    probs = _mix()[:4] if precision == 0 else _mix()
+    res, st, _ = _batch(U, probs, precision=precision, lanczos_basis=basis)
+    for p, r, s in zip(probs, res, st):
+        with U.usbs_create(p, max_iters=CAP, precision=precision, lanczos_basis=basis) as c:
+            solo = U.usbs_solve(c, tol=TOL)
+        assert s in (U.USBS_OK, U.USBS_ENOTCONV)
+        assert r["converged"] == solo["converged"], (p.name, r["iters"], solo["iters"])
+        if r["converged"]:
+            # both pass |f - <C,X>| <= tol (1 + |<C,X>|) in scaled units, so their <C,X>
+            # can differ by at most about twice that
+            assert r["last"]["relgap"] <= TOL and r["last"]["relinf"] <= TOL
+            a, b = r["last"]["cx"], solo["last"]["cx"]
+            assert abs(a - b) <= 2 * TOL * (1 + abs(b)), (p.name, a, b)
+
+
+def test_batched_bipartite_torus_closed_form(mods):
+    """All weights +1 on an even torus: bipartite, so the SDP value is |E| exactly."""
+    torch, U = mods
+    probs = [I.maxcut_torus(s, signed=False) for s in (8, 10, 12)]
+    ctxs = [U.usbs_create(p, max_iters=3000, rho=0.1, ipm_mu_tol=1e-10, lanczos_restarts=50,
+                          lanczos_basis=32) for p in probs]
+    try:
+        res, st = U.usbs_batch_solve(ctxs, tol=1e-5)
+    finally:
+        for c in ctxs:
+            c.close()
+    for p, r in zip(probs, res):
+        e = 2 * p.n
+        last = r["last"]
+        assert r["converged"], (p.name, r["iters"], last["relgap"], last["relinf"])
+        assert last["dual_bound"] >= e * (1 - 1e-5)
+        assert abs(last["objective"] - e) <= 2e-4 * e, (p.name, last["objective"], e)
+
+
+def test_ineligible_context_falls_back(mods):
+    """A basis the kernel is not built for (J = 16) is solved by the per-step path in the
+    same call, and its result equals usbs_solve."""
+    torch, U = mods
+    probs = _mix()[:3]
+    ctxs = [U.usbs_create(p, max_iters=CAP, lanczos_basis=(16 if i == 1 else 32))
+            for i, p in enumerate(probs)]
+    try:
+        res, st = U.usbs_batch_solve(ctxs, tol=TOL)
+    finally:
+        for c in ctxs:
+            c.close()
+    with U.usbs_create(probs[1], max_iters=CAP, lanczos_basis=16) as c:
+        solo = U.usbs_solve(c, tol=TOL)
+    assert res[1]["iters"] == solo["iters"]
+    assert res[1]["last"]["objective"] == solo["last"]["objective"]

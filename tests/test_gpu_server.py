@@ -21,12 +21,15 @@ def mods():
     return gpu_modules()
 
 
+CAP = 600
+
+
 def _probs():
-    return [I.maxcut_er(150 + 20 * s, 5.0, seed=s) for s in range(4)]
+    return [I.maxcut_torus(side, seed=side, signed=True) for side in (12, 14, 16, 18)]
 
 
 def _solo(U, prob):
-    with U.usbs_create(prob) as ctx:
+    with U.usbs_create(prob, max_iters=CAP) as ctx:
         return U.usbs_solve(ctx, tol=TOL)
 
 
@@ -34,7 +37,7 @@ def test_batch_solve_matches_solo(mods):
     torch, U = mods
     probs = _probs()
     solo = [_solo(U, p) for p in probs]
-    ctxs = [U.usbs_create(p) for p in probs]
+    ctxs = [U.usbs_create(p, max_iters=CAP) for p in probs]
     try:
         res, st = U.usbs_batch_solve(ctxs, tol=TOL, max_concurrency=4)
     finally:
@@ -51,7 +54,7 @@ def test_server_matches_solo(mods):
     torch, U = mods
     probs = _probs()
     solo = [_solo(U, p) for p in probs]
-    with U.usbs_server_create(max_slots=3, cache_entries=2, solver={"r": 0}) as srv:
+    with U.usbs_server_create(max_slots=3, cache_entries=2, solver={"r": 0, "max_iters": CAP}) as srv:
         for i, p in enumerate(probs):
             U.usbs_server_submit(srv, i, p, tol=TOL)
         done, t0 = [], time.time()
@@ -71,7 +74,7 @@ def test_grow_keeps_dual_and_warm_solve_agrees(mods):
     torch, U = mods
     parent = I.maxcut_rgg(400, 10.0, seed=5)
     child = I.grow_rgg(parent, frac=0.01, seed=6)
-    with U.usbs_create(parent) as pc:
+    with U.usbs_create(parent, max_iters=CAP) as pc:
         pres = U.usbs_solve(pc, tol=TOL)
         assert pres["converged"]
         y0 = U.usbs_get_dual(pc)
@@ -92,7 +95,7 @@ def test_server_warm_start_from_parent(mods):
     torch, U = mods
     parent = I.maxcut_rgg(400, 10.0, seed=5)
     child = I.grow_rgg(parent, frac=0.01, seed=6)
-    with U.usbs_server_create(max_slots=2, cache_entries=4, solver={"r": 0}) as srv:
+    with U.usbs_server_create(max_slots=2, cache_entries=4, solver={"r": 0, "max_iters": CAP}) as srv:
         U.usbs_server_submit(srv, 1, parent, tol=TOL)
         first = U.usbs_server_poll(srv, 4, wait_ms=60000)
         U.usbs_server_submit(srv, 2, child, parent_id=1, tol=TOL)
