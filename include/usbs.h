@@ -239,14 +239,17 @@ int usbs_op_sketch_update(usbs_ctx* ctx, const void* V_dev, const double* S_dev,
  * kinds below (the events add a few microseconds of host time per launch).
  * --------------------------------------------------------------------------------- */
 #define USBS_KIND_SPMM      0  /* (C - A*(y)) X, the Lanczos matvec */
-#define USBS_KIND_REORTH    1  /* Gram-Schmidt projections, block update, Cholesky-QR apply */
+#define USBS_KIND_REORTH    1  /* Gram-Schmidt projection H = Q^T W (and V^T C V) */
 #define USBS_KIND_RESTART   2  /* thick-restart and Ritz-vector products Q Y */
 #define USBS_KIND_CONSTR    3  /* per-constraint kernels: G^T G, A(V S V^T), alternation */
-#define USBS_KIND_SMALL     4  /* one-CTA FP64 kernels: Ritz, IPM, Cholesky, model value */
+#define USBS_KIND_SMALL     4  /* one-CTA FP64 kernels: IPM, Cholesky-QR factor, model value */
 #define USBS_KIND_REDUCE    5  /* cross-CTA reductions */
 #define USBS_KIND_SKETCH    6  /* V^T Psi and the sketch update */
 #define USBS_KIND_SETUP     7  /* operator set-up for a new y */
-#define USBS_NUM_KINDS      8
+#define USBS_KIND_REORTH_UPDATE 8  /* X = W - Q H with H2 = Q^T X and X^T X (second pass) */
+#define USBS_KIND_REORTH_FINAL  9  /* (X - Q H2) R^-1: the new orthonormal block */
+#define USBS_KIND_RITZ      10 /* Rayleigh-Ritz of the projected J x J matrix (one CTA) */
+#define USBS_NUM_KINDS      11
 
 /* Turn event timing on (1) or off (0); turning it on clears the totals. */
 int usbs_profile(usbs_ctx* ctx, int on);
@@ -288,8 +291,8 @@ int usbs_sketch_update_static(int64_t n, int r, const float* V_dev, const double
  * Serving and batching.  The paper has no counterpart for these: they are the service
  * forms built around its solver.  Requests enter a FIFO queue; one is admitted when a
  * solve slot is free and its device footprint fits the memory budget.  Each slot is a
- * host thread with its own CUDA stream, so admitted solves overlap on the GPU
- * (continuous batching).  Finished instances stay device-resident in an LRU cache; a
+ * host thread and each instance owns a CUDA stream, so admitted solves overlap on the
+ * GPU (continuous batching).  Finished instances stay device-resident in an LRU cache; a
  * request that names a cached instance as its parent is warm-started from it with
  * usbs_grow, as the paper warm-starts grown instances (Sec. 5.1).
  * --------------------------------------------------------------------------------- */

@@ -183,7 +183,8 @@ __device__ int b_step(BatchCtx<T>& b, T*& V, T*& Vnew, double*& ax, double*& axn
   __syncthreads();
   int n_alt;
   for (n_alt = 1; n_alt <= d->max_alt; ++n_alt) {
-    k_ipm_dev(sc, red, d->kc, d->alpha, d->rho, d->ipm_mu_tol, d->ipm_max_iter, n_alt == 1);
+    if (threadIdx.x < 32)
+      k_ipm_dev(sc, red, d->kc, d->alpha, d->rho, d->ipm_mu_tol, d->ipm_max_iter, n_alt == 1);
     __syncthreads();
     if (!d->any_ineq) break;
     k_alt_dev<T>(0, 1, m, d->con_ptr, d->ent_i, d->ent_j, (const T*)d->ent_v, V, sc, ax, d->y,

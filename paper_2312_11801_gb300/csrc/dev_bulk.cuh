@@ -203,9 +203,9 @@ __device__ __forceinline__ void k_gstats_dev(const int cta, const int ncta, int 
   }
 }
 
-// Block reduction of NV doubles per thread into partials[blockIdx][0..NV).
+// Block reduction of NV doubles per thread into partials[cta][0..NV).
 template <int NV>
-__device__ __forceinline__ void block_reduce_store(double (&v)[NV], double* USBS_RESTRICT partials,
+__device__ __forceinline__ void block_reduce_store(const int cta, double (&v)[NV], double* USBS_RESTRICT partials,
                                                    double* sred /* 8 x NV */) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
@@ -221,7 +221,7 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[NV], double* USBS
   for (int t = threadIdx.x; t < NV; t += blockDim.x) {
     double s = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sred[w * NV + t];
-    partials[(size_t)blockIdx.x * PART_STRIDE + t] = s;
+    partials[(size_t)cta * PART_STRIDE + t] = s;
   }
 }
 
@@ -293,7 +293,7 @@ __device__ __forceinline__ void k_xupdate_dev(const int cta, const int ncta, int
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if (lane == 0) smax[warp] = mx;
-  block_reduce_store<39>(acc, partials, sred);
+  block_reduce_store<39>(cta, acc, partials, sred);
   if (threadIdx.x == 0) {
     double m2 = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m2 = fmax(m2, smax[w]);
@@ -343,7 +343,7 @@ __device__ __forceinline__ void k_alt_dev(const int cta, const int ncta, int m, 
     acc[36] += ax[c] * wc;
     acc[37] += dn * dn;
   }
-  block_reduce_store<38>(acc, partials, sred);
+  block_reduce_store<38>(cta, acc, partials, sred);
 }
 
 // ---- z = A(V S V^T) --------------------------------------------------------------------

@@ -575,49 +575,52 @@ __device__ __forceinline__ double aug_at(const double* aug, int r, int c) {
   return aug[idx * 16 + (r % 4) * 4 + (c % 4)];
 }
 
+// One warp runs the whole IPM: every step of a Newton iteration is a lane-strided loop
+// over k-sized data in shared memory, ordered by __syncwarp only.  The FP64 work of an
+// iteration is about 26K multiply-adds (dominated by the 36 x 36 elimination), so on
+// GB300's FP64 rate the iteration is bound by that arithmetic, not by CTA barriers.
+// Callers run it on lanes 0..31 of one warp (the per-step kernel launches 32 threads).
 __device__ __forceinline__ void k_ipm_dev(DevScalars* sc, const double* USBS_RESTRICT red, int kc,
-                                             double alpha, double rho, double mu_tol, int max_iter,
-                                             int first_pass) {
+                                          double alpha, double rho, double mu_tol, int max_iter,
+                                          int first_pass) {
   __shared__ IpmShared sh;
-  const int tid = threadIdx.x;
+  __shared__ int pq[KSV][2];   // svec position u -> (p, q), p >= q, column-major lower triangle
+  const int lane = threadIdx.x & 31;
   const int K = kc * (kc + 1) / 2;
   const double* aug = red + RED_AUG;
   const double* vec = red + RED_VEC;
   const double* vc = red + RED_VC;
-  if (tid == 0) {
+  if (lane == 0) {
     int u = 0;
     for (int q = 0; q < kc; ++q)
-      for (int p = q; p < kc; ++p) sh.map[u++] = svec_idx8(p, q);
+      for (int p = q; p < kc; ++p) {
+        sh.map[u] = svec_idx8(p, q);
+        pq[u][0] = p;
+        pq[u][1] = q;
+        ++u;
+      }
     sh.has_eta = sc->tr > 0.0 ? 1 : 0;
     sc->has_eta = sh.has_eta;
   }
-  __syncthreads();
+  __syncwarp();
   const int has_eta = sh.has_eta;
   const double tr = sc->tr, cx = sc->cx;
   const double a2r = alpha * alpha / rho;
-  for (int t = tid; t < K * K; t += blockDim.x) {
+  for (int t = lane; t < K * K; t += 32) {
     const int i = t / K, j = t % K;
     sh.Q[t] = a2r * aug_at(aug, sh.map[i], sh.map[j]);
   }
-  if (tid < K) {
-    const int gi = sh.map[tid];
-    sh.q12[tid] = has_eta ? a2r / tr * aug_at(aug, gi, 36) : 0.0;
+  for (int u = lane; u < K; u += 32) {
+    const int gi = sh.map[u];
+    sh.q12[u] = has_eta ? a2r / tr * aug_at(aug, gi, 36) : 0.0;
     const double gtw = first_pass ? aug_at(aug, gi, 37) : vec[gi];
-    // svec of V^T C V (k_c x k_c block)
-    int p = 0, q = 0;
-    {
-      int u = tid;
-      for (q = 0; q < kc; ++q) {
-        if (u < kc - q) { p = q + u; break; }
-        u -= kc - q;
-      }
-    }
+    const int p = pq[u][0], q = pq[u][1];
     const double vcpq = 0.5 * (vc[p * 8 + q] + vc[q * 8 + p]);
     const double svc = (p == q) ? vcpq : SQ2 * vcpq;
-    sh.h1[tid] = alpha * (gtw - svc);
-    sh.v[tid] = (p == q) ? 1.0 : 0.0;
+    sh.h1[u] = alpha * (gtw - svc);
+    sh.v[u] = (p == q) ? 1.0 : 0.0;
   }
-  if (tid == 0) {
+  if (lane == 0) {
     sh.q22 = has_eta ? a2r / (tr * tr) * aug_at(aug, 36, 36) : 0.0;
     const double axw = first_pass ? aug_at(aug, 36, 37) : vec[36];
     sh.h2 = has_eta ? alpha * (axw - cx) / tr : 0.0;
@@ -634,51 +637,37 @@ __device__ __forceinline__ void k_ipm_dev(DevScalars* sc, const double* USBS_RES
     sh.done = 0;
     sh.iters = 0;
   }
-  __syncthreads();
-  const int lane = tid & 31, warp = tid >> 5;
+  __syncwarp();
+  const int LDL = K + 1;
   for (int it = 1; it <= max_iter; ++it) {
     // S^-1 (warp-cooperative Cholesky and inverse)
-    if (warp == 0) {
-      warp_chol(sh.S, sh.Lc, kc);
-      warp_spd_inverse(sh.Lc, sh.work, sh.Sinv, kc);
-    }
-    __syncthreads();
-    if (tid < K) {
-      int p = 0, q = 0;
-      int u = tid;
-      for (q = 0; q < kc; ++q) {
-        if (u < kc - q) { p = q + u; break; }
-        u -= kc - q;
-      }
+    warp_chol(sh.S, sh.Lc, kc);
+    warp_spd_inverse(sh.Lc, sh.work, sh.Sinv, kc);
+    for (int u = lane; u < K; u += 32) {
+      const int p = pq[u][0], q = pq[u][1];
       const double f = (p == q) ? 1.0 : SQ2;
-      sh.s[tid] = f * sh.S[p * 8 + q];
-      sh.t[tid] = f * sh.T[p * 8 + q];
-      sh.sinv[tid] = f * sh.Sinv[p * 8 + q];
+      sh.s[u] = f * sh.S[p * 8 + q];
+      sh.t[u] = f * sh.T[p * 8 + q];
+      sh.sinv[u] = f * sh.Sinv[p * 8 + q];
     }
     // T (x)_s S^-1 entry by entry: (1/(s_a s_b)) (H_jk G_il + G_jk H_il + H_jl G_ik + G_jl H_ik)
     // with G = T, H = S^-1, a = (i, j), b = (k, l), s = 2 on the diagonal and sqrt(2) off it
-    for (int t = tid; t < K * K; t += blockDim.x) {
+    for (int t = lane; t < K * K; t += 32) {
       const int ra = t / K, cb = t % K;
-      int i = 0, j = 0, k = 0, l = 0;
-      {
-        int u = ra;
-        for (j = 0; j < kc; ++j) { if (u < kc - j) { i = j + u; break; } u -= kc - j; }
-        u = cb;
-        for (l = 0; l < kc; ++l) { if (u < kc - l) { k = l + u; break; } u -= kc - l; }
-      }
+      const int i = pq[ra][0], j = pq[ra][1], k = pq[cb][0], l = pq[cb][1];
       const double inv_s = ((i == j) ? 0.5 : 1.0 / SQ2) * ((k == l) ? 0.5 : 1.0 / SQ2);
       const double* G = sh.T;
       const double* H = sh.Sinv;
       sh.TS[t] = (H[j * 8 + k] * G[i * 8 + l] + G[j * 8 + k] * H[i * 8 + l] +
                   H[j * 8 + l] * G[i * 8 + k] + G[j * 8 + l] * H[i * 8 + k]) * inv_s;
     }
-    __syncthreads();
-    if (tid < K) {
-      double f1 = sh.h1[tid] - sh.t[tid] + sh.omega * sh.v[tid] + sh.eta * sh.q12[tid];
-      for (int c = 0; c < K; ++c) f1 += sh.Q[tid * K + c] * sh.s[c];
-      sh.F1[tid] = f1;
+    __syncwarp();
+    for (int u = lane; u < K; u += 32) {
+      double f1 = sh.h1[u] - sh.t[u] + sh.omega * sh.v[u] + sh.eta * sh.q12[u];
+      for (int c = 0; c < K; ++c) f1 += sh.Q[u * K + c] * sh.s[c];
+      sh.F1[u] = f1;
     }
-    if (tid == 32) {
+    if (lane == 0) {
       double trS = 0.0;
       for (int p = 0; p < kc; ++p) trS += sh.S[p * 8 + p];
       const double slack = 1.0 - trS - sh.eta;
@@ -693,12 +682,12 @@ __device__ __forceinline__ void k_ipm_dev(DevScalars* sc, const double* USBS_RES
         sh.det = sh.kappa1 * sh.kappa2 + 1.0;
       }
     }
-    __syncthreads();
+    __syncwarp();
     // assemble [L | rhs] (eq. delta_S_linear_system2)
     {
       const double idet = has_eta ? 1.0 / sh.det : 0.0, ik1 = has_eta ? 0.0 : 1.0 / sh.kappa1;
-      for (int t = tid; t < K * (K + 1); t += blockDim.x) {
-        const int i = t / (K + 1), j = t % (K + 1);
+      for (int t = lane; t < K * LDL; t += 32) {
+        const int i = t / LDL, j = t % LDL;
         double val;
         if (j < K) {
           val = sh.Q[i * K + j] + sh.TS[i * K + j];
@@ -717,63 +706,55 @@ __device__ __forceinline__ void k_ipm_dev(DevScalars* sc, const double* USBS_RES
         sh.L[t] = val;
       }
     }
-    __syncthreads();
+    if (lane == 0) sh.piv = 0;
+    __syncwarp();
     // Gaussian elimination with partial pivoting
-    const int LDL = K + 1;
-    if (tid == 0) sh.piv = 0;
-    __syncthreads();
     for (int p = 0; p < K; ++p) {
-      if (warp == 0) {
-        double best = -1.0;
-        int bi = p;
-        for (int r = p + lane; r < K; r += 32) {
-          const double x = fabs(sh.L[r * LDL + p]);
-          if (x > best) { best = x; bi = r; }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-          const double ob = __shfl_xor_sync(FULL, best, o);
-          const int oi = __shfl_xor_sync(FULL, bi, o);
-          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-        }
-        if (bi != p)
-          for (int c = p + lane; c < LDL; c += 32) {
-            const double x = sh.L[p * LDL + c];
-            sh.L[p * LDL + c] = sh.L[bi * LDL + c];
-            sh.L[bi * LDL + c] = x;
-          }
-        __syncwarp();
-        if (lane == 0) {
-          // an exactly singular system (possible at degenerate optima): mark the
-          // direction unusable instead of dividing by zero
-          const double pv = sh.L[p * LDL + p];
-          sh.fcol[p] = (fabs(pv) > 1e-300) ? 1.0 / pv : 0.0;
-          if (!(fabs(pv) > 1e-300)) sh.piv = -1;
-        }
+      double best = -1.0;
+      int bi = p;
+      for (int r = p + lane; r < K; r += 32) {
+        const double x = fabs(sh.L[r * LDL + p]);
+        if (x > best) { best = x; bi = r; }
       }
-      __syncthreads();
-      const double ipv = sh.fcol[p];
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(FULL, best, o);
+        const int oi = __shfl_xor_sync(FULL, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (bi != p)
+        for (int c = p + lane; c < LDL; c += 32) {
+          const double x = sh.L[p * LDL + c];
+          sh.L[p * LDL + c] = sh.L[bi * LDL + c];
+          sh.L[bi * LDL + c] = x;
+        }
+      __syncwarp();
+      // an exactly singular system (possible at degenerate optima): mark the direction
+      // unusable instead of dividing by zero
+      const double pv = sh.L[p * LDL + p];
+      const double ipv = (fabs(pv) > 1e-300) ? 1.0 / pv : 0.0;
+      if (lane == 0) {
+        sh.fcol[p] = ipv;
+        if (!(fabs(pv) > 1e-300)) sh.piv = -1;
+      }
       const int rows = K - p - 1, cols = LDL - p - 1;
-      for (int t = tid; t < rows * cols; t += blockDim.x) {
+      for (int t = lane; t < rows * cols; t += 32) {
         const int r = p + 1 + t / cols, c = p + 1 + t % cols;
         sh.L[r * LDL + c] -= sh.L[r * LDL + p] * ipv * sh.L[p * LDL + c];
       }
-      __syncthreads();
+      __syncwarp();
     }
-    // back substitution (warp 0) with the reciprocal pivots kept in fcol
-    if (warp == 0) {
-      for (int r = K - 1; r >= 0; --r) {
-        double x = 0.0;
-        if (lane == 0) {
-          x = sh.L[r * LDL + K] * sh.fcol[r];
-          sh.ds[r] = x;
-        }
-        x = __shfl_sync(FULL, x, 0);
-        for (int i = lane; i < r; i += 32) sh.L[i * LDL + K] -= sh.L[i * LDL + r] * x;
-        __syncwarp();
+    // back substitution with the reciprocal pivots kept in fcol
+    for (int r = K - 1; r >= 0; --r) {
+      double x = 0.0;
+      if (lane == 0) {
+        x = sh.L[r * LDL + K] * sh.fcol[r];
+        sh.ds[r] = x;
       }
+      x = __shfl_sync(FULL, x, 0);
+      for (int i = lane; i < r; i += 32) sh.L[i * LDL + K] -= sh.L[i * LDL + r] * x;
+      __syncwarp();
     }
-    __syncthreads();
-    if (tid == 0) {
+    if (lane == 0) {
       double vds = 0.0;
       for (int c = 0; c < K; ++c) vds += sh.v[c] * sh.ds[c];
       if (has_eta) {
@@ -789,25 +770,24 @@ __device__ __forceinline__ void k_ipm_dev(DevScalars* sc, const double* USBS_RES
         sh.dzeta = 0.0;
       }
     }
-    if (tid >= 32 && tid < 32 + K) {
-      const int r = tid - 32;
+    for (int r = lane; r < K; r += 32) {
       double x = sh.mu * sh.sinv[r] - sh.t[r];
       for (int c = 0; c < K; ++c) x -= sh.TS[r * K + c] * sh.ds[c];
       sh.dt[r] = x;
     }
-    __syncthreads();
+    __syncwarp();
     // a non-finite Newton direction (singular system): keep the current strictly
     // feasible iterate and stop
-    if (tid == 0) {
+    if (lane == 0) {
       bool fin = isfinite(sh.deta) && isfinite(sh.domega) && isfinite(sh.dzeta) && sh.piv >= 0;
       for (int c = 0; c < K && fin; ++c) fin = isfinite(sh.ds[c]) && isfinite(sh.dt[c]);
       sh.done = fin ? 0 : 2;
     }
-    __syncthreads();
+    __syncwarp();
     if (sh.done == 2) break;
-    if (tid < 64) {
+    for (int t = lane; t < 64; t += 32) {
       // smat of ds, dt
-      const int p = tid / 8, q = tid % 8;
+      const int p = t / 8, q = t % 8;
       double vs = 0.0, vt = 0.0;
       if (p < kc && q < kc) {
         const int pi = max(p, q), qi = min(p, q);
@@ -816,58 +796,48 @@ __device__ __forceinline__ void k_ipm_dev(DevScalars* sc, const double* USBS_RES
         vs = f * sh.ds[u];
         vt = f * sh.dt[u];
       }
-      sh.dS[tid] = vs;
-      sh.dT[tid] = vt;
+      sh.dS[t] = vs;
+      sh.dT[t] = vt;
     }
-    if (tid == 0) sh.delta = 1.0;
-    __syncthreads();
-    // backtracking: halve until strictly feasible (warps 0 and 1 test S and T), then 0.95 delta
+    if (lane == 0) sh.delta = 1.0;
+    __syncwarp();
+    // backtracking: halve until S and T are positive definite and the scalars and trace
+    // slack positive, then take 0.95 delta
     for (int ls = 0; ls < 80; ++ls) {
       const double delta = sh.delta;
-      if (tid < 64) {
-        const int p = tid / 8, q = tid % 8;
-        sh.St[tid] = sh.S[tid] + delta * sh.dS[tid];
-        sh.Tt[tid] = sh.T[tid] + delta * sh.dT[tid];
-        (void)p; (void)q;
+      for (int t = lane; t < 64; t += 32) {
+        sh.St[t] = sh.S[t] + delta * sh.dS[t];
+        sh.Tt[t] = sh.T[t] + delta * sh.dT[t];
       }
-      __syncthreads();
-      bool okw = true;
-      if (warp == 0) okw = warp_chol(sh.St, nullptr, kc);
-      if (warp == 1) okw = warp_chol(sh.Tt, nullptr, kc);
-      if (lane == 0 && warp < 2) sh.fcol[warp] = okw ? 1.0 : 0.0;
-      __syncthreads();
-      if (tid == 0) {
+      __syncwarp();
+      const bool okS = warp_chol(sh.St, nullptr, kc);
+      const bool okT = warp_chol(sh.Tt, nullptr, kc);
+      if (lane == 0) {
         double trS = 0.0;
         for (int p = 0; p < kc; ++p) trS += sh.St[p * 8 + p];
         const double en = sh.eta + delta * sh.deta, zn = sh.zeta + delta * sh.dzeta;
         const double on = sh.omega + delta * sh.domega;
-        bool ok = on > 0.0 && (1.0 - trS - en) > 0.0 && sh.fcol[0] > 0.5 && sh.fcol[1] > 0.5;
+        bool ok = on > 0.0 && (1.0 - trS - en) > 0.0 && okS && okT;
         if (has_eta) ok = ok && en > 0.0 && zn > 0.0;
         sh.done = ok ? 1 : 0;
         if (!ok) sh.delta = 0.5 * delta;
       }
-      __syncthreads();
+      __syncwarp();
       if (sh.done) break;
     }
-    __syncthreads();
     const double delta = 0.95 * sh.delta;
-    if (tid < 64) {
-      const int p = tid / 8, q = tid % 8;
-      double sv = sh.S[tid], tv = sh.T[tid];
+    for (int t = lane; t < 64; t += 32) {
+      const int p = t / 8, q = t % 8;
+      double sv = sh.S[t], tv = sh.T[t];
       if (p < kc && q < kc) {
-        sv = sh.S[tid] + 0.5 * delta * (sh.dS[p * 8 + q] + sh.dS[q * 8 + p]);
-        tv = sh.T[tid] + 0.5 * delta * (sh.dT[p * 8 + q] + sh.dT[q * 8 + p]);
+        sv = sh.S[t] + 0.5 * delta * (sh.dS[p * 8 + q] + sh.dS[q * 8 + p]);
+        tv = sh.T[t] + 0.5 * delta * (sh.dT[p * 8 + q] + sh.dT[q * 8 + p]);
       }
-      sh.St[tid] = sv;
-      sh.Tt[tid] = tv;
+      sh.S[t] = sv;
+      sh.T[t] = tv;
     }
-    __syncthreads();
-    if (tid < 64) {
-      sh.S[tid] = sh.St[tid];
-      sh.T[tid] = sh.Tt[tid];
-    }
-    __syncthreads();
-    if (tid == 0) {
+    __syncwarp();
+    if (lane == 0) {
       sh.omega += delta * sh.domega;
       if (has_eta) {
         sh.eta += delta * sh.deta;
@@ -885,10 +855,10 @@ __device__ __forceinline__ void k_ipm_dev(DevScalars* sc, const double* USBS_RES
       sh.iters = it;
       sh.done = (sh.mu < mu_tol || !isfinite(sh.mu)) ? 1 : 0;
     }
-    __syncthreads();
+    __syncwarp();
     if (sh.done) break;
   }
-  if (tid == 0) {
+  if (lane == 0) {
     for (int u = 0; u < 64; ++u) {
       sc->S_hat[u] = sh.S[u];
       sc->S[u] = alpha * sh.S[u];
@@ -901,6 +871,7 @@ __device__ __forceinline__ void k_ipm_dev(DevScalars* sc, const double* USBS_RES
     sc->ipm_iters += sh.iters;
     if (!isfinite(sh.mu) || !isfinite(sh.eta)) sc->status = USBS_ENUMERIC;
   }
+  __syncwarp();
 }
 
 // ---- model value, descent test, implicit primal update and gates ------------------------------

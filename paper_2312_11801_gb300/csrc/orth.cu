@@ -99,7 +99,7 @@ void Orth<T>::gram_xy(Ctx* c, const void* X, const void* Y) {
 
 template <typename T>
 void Orth<T>::update(Ctx* c, const void* Qb, int nb, void* W, const int* mask) {
-  USBS_LAUNCH_B(c, USBS_KIND_REORTH, mask ? 0.0 : 8.0 * sizeof(T) * c->n * (nb + 2));
+  USBS_LAUNCH_B(c, USBS_KIND_REORTH_UPDATE, mask ? 0.0 : 8.0 * sizeof(T) * c->n * (nb + 2));
   set_attrs<T>();
   const size_t sm = std::max(tile_smem<T>(nb, 8 * 64), sizeof(double) * 8 * 576);
   k_tupdate<T><<<orth_grid(c, c->n), 256, sm, c->stream>>>((int)c->n, (const T*)Qb, (size_t)c->n * 8,
@@ -109,7 +109,7 @@ void Orth<T>::update(Ctx* c, const void* Qb, int nb, void* W, const int* mask) {
 template <typename T>
 void Orth<T>::finalize(Ctx* c, const void* Qb, int nb, const void* W, void* out, const int* mask,
                        uint64_t seed) {
-  USBS_LAUNCH_B(c, USBS_KIND_REORTH, mask ? 0.0 : 8.0 * sizeof(T) * c->n * (nb + 2));
+  USBS_LAUNCH_B(c, USBS_KIND_REORTH_FINAL, mask ? 0.0 : 8.0 * sizeof(T) * c->n * (nb + 2));
   set_attrs<T>();
   const size_t sm = tile_smem<T>(nb, 8 * 64 + 64);
   k_tfinalize<T><<<orth_grid(c, c->n), 256, sm, c->stream>>>(

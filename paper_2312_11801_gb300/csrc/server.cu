@@ -4,7 +4,8 @@
 // device footprint (usbs_instance_bytes) fits the memory budget; finished instances stay
 // resident in an LRU cache so that a later request naming one of them as its parent is
 // warm-started from it with usbs_grow (the paper's warm start, Sec. 5.1).  Each slot is a
-// host thread with its own CUDA stream, so admitted solves overlap on the device.  In
+// host thread and each context owns its CUDA stream, so admitted solves overlap on the
+// device.  In
 // dry-run mode no CUDA call is made and a request occupies its slot for the service time
 // the caller gives, which lets the scheduling be tested without a GPU.
 #include <algorithm>
@@ -20,10 +21,6 @@
 #include <vector>
 
 #include "common.cuh"
-
-namespace usbs {
-void ctx_set_stream(usbs_ctx* ctx, cudaStream_t s);
-}
 
 namespace {
 
@@ -132,11 +129,7 @@ struct usbs_server {
   }
 
   void worker(int slot) {
-    cudaStream_t stream = nullptr;
-    if (!p.dry_run) {
-      if (p.solver.device >= 0) cudaSetDevice(p.solver.device);
-      cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
-    }
+    if (!p.dry_run && p.solver.device >= 0) cudaSetDevice(p.solver.device);
     for (;;) {
       std::unique_ptr<Req> r;
       {
@@ -159,14 +152,16 @@ struct usbs_server {
         std::this_thread::sleep_for(std::chrono::duration<double>(r->fake_s));
         c.status = USBS_OK;
       } else {
+        // every context owns its stream (created by usbs_create or usbs_grow, destroyed
+        // with the context), so resident instances never outlive the stream they use and
+        // solves of different requests overlap on the device
         usbs_params sp = p.solver;
-        sp.stream = stream;
+        sp.stream = nullptr;
         int rc = USBS_OK;
         if (r->parent_ctx) {
           rc = usbs_grow(r->parent_ctx, &ctx, r->n, r->rowptr.data(), r->col.data(), r->val.data(),
                          r->m, r->nnzA, r->acon.data(), r->ai.data(), r->aj.data(), r->aval.data(),
                          r->b.data(), r->ineq.data(), r->psi.empty() ? nullptr : r->psi.data());
-          if (rc == USBS_OK) usbs::ctx_set_stream(ctx, stream);
           c.warm = rc == USBS_OK ? 1 : 0;
         }
         if (!c.warm) {   // cold start, also when the problem does not extend the parent
@@ -215,7 +210,6 @@ struct usbs_server {
       }
       cv_done.notify_all();
     }
-    if (stream) cudaStreamDestroy(stream);
   }
 };
 
@@ -236,15 +230,6 @@ static uint64_t instance_bytes(int64_t n, int64_t nnz_off, int64_t m, int64_t nn
   b += 8.0 * n * r;                                                             // P, Psi
   b += 8.0 * (RED_GRID_MAX * PART_STRIDE + RED_TOTAL) + 2.0 * (sizeof(DevScalars) + sizeof(DevLanczos));
   return (uint64_t)(b * 1.02 + (1 << 20));                                      // + allocation slack
-}
-
-void ctx_set_stream(usbs_ctx* ctx, cudaStream_t s) {
-  Ctx* c = reinterpret_cast<Ctx*>(ctx);
-  cudaStreamSynchronize(c->stream);
-  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
-  c->stream = s;
-  c->own_stream = false;
-  c->prm.stream = s;
 }
 
 }  // namespace usbs

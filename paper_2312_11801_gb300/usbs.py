@@ -14,7 +14,8 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libusbs.so"
 
 USBS_OK, USBS_EINVAL, USBS_ENOMEM, USBS_ECUDA = 0, -1, -2, -3
 USBS_ETIMEOUT, USBS_ENOTCONV, USBS_EBUSY, USBS_ENUMERIC = -4, -5, -6, -7
-KINDS = ["spmm", "reorth", "restart", "constraint", "small_fp64", "reduce", "sketch", "setup"]
+KINDS = ["spmm", "reorth", "restart", "constraint", "small_fp64", "reduce", "sketch", "setup",
+         "reorth_update", "reorth_final", "ritz"]
 PRECISION_FP64, PRECISION_MIXED = 0, 1
 _ERR = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "ENOTCONV",
         -6: "EBUSY", -7: "ENUMERIC"}
