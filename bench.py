@@ -310,7 +310,7 @@ def _pct(xs, q):
     return float(np.percentile(np.asarray(xs, dtype=np.float64), q)) if len(xs) else None
 
 
-def plain_fp64_sample(U, probs, rho, tol, max_iters, budget_s):
+def plain_fp64_sample(U, probs, rho, tol, max_iters, budget_s, basis=32):
     """The plain path: one instance at a time, FP64 throughout, per-step kernels, cold
     start; solves in order until the time budget is spent.  Returns per-solve records."""
     out = []
@@ -319,7 +319,8 @@ def plain_fp64_sample(U, probs, rho, tol, max_iters, budget_s):
         if out and time.perf_counter() - t_all > budget_s:
             break
         t0 = time.perf_counter()
-        with U.usbs_create(p, precision=U.PRECISION_FP64, rho=rho, max_iters=max_iters) as c:
+        with U.usbs_create(p, precision=U.PRECISION_FP64, rho=rho, max_iters=max_iters,
+                           lanczos_basis=basis) as c:
             r = U.usbs_solve(c, tol=tol)
         out.append({"secs": time.perf_counter() - t0, "iters": r["iters"], "converged": r["converged"],
                     "n": p.n})
@@ -337,7 +338,8 @@ def run_batched(args, world, rank, local, pg):
     from paper_2312_11801_gb300 import instances as I
     torch.cuda.set_device(local)
     probs = I.batched_er(args.batch_count, seed0=1000 * rank)
-    kw = dict(precision=U.PRECISION_MIXED, lanczos_basis=32, rho=args.rho, max_iters=args.max_iters)
+    kw = dict(precision=U.PRECISION_MIXED, lanczos_basis=args.lanczos_basis, rho=args.rho,
+              max_iters=args.max_iters)
     ctxs = [U.usbs_create(p, **kw) for p in probs]
     for _ in range(args.warmup):
         U.usbs_batch_solve(ctxs, tol=TOL)
@@ -366,7 +368,8 @@ def run_batched(args, world, rank, local, pg):
         c.close()
     e2e_conv = sum(r["converged"] for r in res)
     e2e_elapsed = max_over_ranks(pg, time.perf_counter() - t0)
-    plain = plain_fp64_sample(U, probs, args.rho, TOL, args.max_iters, args.plain_budget) \
+    plain = plain_fp64_sample(U, probs, args.rho, TOL, args.max_iters, args.plain_budget,
+                              args.lanczos_basis) \
         if rank == 0 and not args.no_plain else []
     pconv = sum(r["converged"] for r in plain)
     line = {
@@ -374,7 +377,7 @@ def run_batched(args, world, rank, local, pg):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": f"batched_er_{args.batch_count}_n100-4000_d8_u01_mixed_J32",
+        "config": {"workload": f"batched_er_{args.batch_count}_n100-4000_d8_u01_mixed_J{args.lanczos_basis}",
                    "instances": len(probs), "rho": args.rho, "tol": TOL, "k_c": 8,
                    "precision": "mixed: FP32 bulk, FP64 k-sized", "launch": "persistent, one CTA per instance",
                    "parallelism": f"replicas{world}", "converged_per_step": conv / args.steps,
@@ -424,7 +427,7 @@ def run_serve(args, world, rank, local, pg):
     for q in reqs:
         t0 = time.perf_counter()
         with U.usbs_create(q["prob"], precision=U.PRECISION_FP64, rho=args.rho,
-                           max_iters=args.max_iters) as c:
+                           max_iters=args.max_iters, lanczos_basis=args.lanczos_basis) as c:
             r = U.usbs_solve(c, tol=TOL)
         plain_s.append((time.perf_counter() - t0, r["converged"]))
     plain_cap = len(reqs) / sum(s for s, _ in plain_s)
@@ -440,7 +443,8 @@ def run_serve(args, world, rank, local, pg):
     plain_makespan = free_at - arrivals[0]
     # served: submit in real time
     srv = U.usbs_server_create(max_slots=args.slots, cache_entries=args.requests,
-                               solver={"rho": args.rho, "lanczos_basis": 32, "max_iters": args.max_iters})
+                               solver={"rho": args.rho, "lanczos_basis": args.lanczos_basis,
+                                       "max_iters": args.max_iters})
     done = []
     t0 = time.perf_counter()
     for q, a in zip(reqs, arrivals):
@@ -461,6 +465,7 @@ def run_serve(args, world, rank, local, pg):
         "config": {"workload": f"serve_rgg_poisson_{args.requests}req_n{args.n_lo}-{args.n_hi}",
                    "requests": len(reqs), "grown_from_parent": sum(q["parent"] >= 0 for q in reqs),
                    "rho": args.rho, "tol": TOL, "load_vs_plain_capacity": args.load,
+                   "lanczos_basis": args.lanczos_basis, "max_iters": args.max_iters,
                    "arrival_rate_per_s": rate, "slots": args.slots},
         "served": {"solves_per_s": conv / served_makespan, "converged": conv,
                    "p50_s": _pct(lat, 50), "p99_s": _pct(lat, 99),
@@ -531,6 +536,60 @@ def run_c1(args, world, rank, local, pg):
         print(json.dumps(line), flush=True)
 
 
+def run_c3(args, world, rank, local, pg):
+    """C3: clustering SDP, n = 65,536 points, 655,360 signed similarity edges (weights
+    N(0, 1)), X_ii = 1 and X_ij >= 0 on every edge (~2.1e9 implicit variables), sketch
+    rank 32, mixed precision.  A step is a cold-start solve, capped at --max-iters."""
+    import torch
+    from paper_2312_11801_gb300 import build as B
+    B.build()
+    from paper_2312_11801_gb300 import usbs as U
+    from paper_2312_11801_gb300 import instances as I
+    torch.cuda.set_device(local)
+    prob = I.clustering_sdp(args.c3_n, args.c3_n * 10, seed=0)
+    psi = I.gaussian_psi(prob.n, 32, seed=1)
+    stream = torch.cuda.Stream()
+    kw = dict(precision=U.PRECISION_MIXED, r=32, rho=args.c3_rho, max_iters=args.max_iters,
+              lanczos_basis=args.lanczos_basis, stream=stream)
+    ctx = U.usbs_create(prob, psi=psi, **kw)
+    for _ in range(args.warmup):
+        U.usbs_solve(ctx, tol=TOL)
+    U.usbs_profile(ctx, True)
+    n0 = U.usbs_launch_count(ctx)
+    barrier(pg)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    res = [U.usbs_solve(ctx, tol=TOL) for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    elapsed = max_over_ranks(pg, e0.elapsed_time(e1) / 1e3)
+    launches = U.usbs_launch_count(ctx) - n0
+    stats = U.usbs_kernel_stats(ctx)
+    U.usbs_profile(ctx, False)
+    ctx.close()
+    total_ms = sum(v[0] for v in stats.values()) or 1.0
+    last = res[-1]["last"]
+    iters = sum(r["iters"] for r in res)
+    line = {
+        "metric": METRIC, "value": world * sum(r["converged"] for r in res) / elapsed, "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"clustering_n{prob.n}_e{args.c3_n * 10}_r32_mixed", "m": prob.m,
+                   "rho": args.c3_rho, "tol": TOL, "lanczos_basis": args.lanczos_basis,
+                   "iters_per_solve": [r["iters"] for r in res],
+                   "converged": [r["converged"] for r in res],
+                   "ms_per_iteration": 1e3 * elapsed / max(iters, 1),
+                   "gates": {"relgap": last["relgap"], "relinf": last["relinf"],
+                             "objective": last["objective"], "dual_bound": last["dual_bound"]}},
+        "gpu_launches": int(launches),
+        "kernel_share": {k: round(v[0] / total_ms, 4) for k, v in stats.items()},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_reference(args, world, rank):
     """The oracle arm: each step is the bounded oracle sample of run_ours's workload."""
     if rank != 0:
@@ -572,7 +631,9 @@ def main():
     ap.add_argument("--lanczos-basis", type=int, default=32, choices=[16, 32, 64],
                     help="Lanczos basis of the C2 solve (the paper's 32 inner iterations)")
     ap.add_argument("--lanczos-tol", type=float, default=0.0, help="0 = the library default")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "batched", "serve"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "batched", "serve"])
+    ap.add_argument("--c3-n", type=int, default=65536)
+    ap.add_argument("--c3-rho", type=float, default=0.01)
     ap.add_argument("--rho", type=float, default=0.1, help="rho of the batched and served workloads")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--plain-budget", type=float, default=60.0)
@@ -589,6 +650,8 @@ def main():
         int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0, None)
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.workload == "c3":
+        run_c3(args, world, rank, local, pg)
     elif args.workload == "c1":
         run_c1(args, world, rank, local, pg)
     elif args.workload == "batched":

@@ -121,7 +121,7 @@ __global__ void k_reduce_max(const double* __restrict__ partials, int nparts, in
 int red_grid(Ctx* c, int64_t rows, int rows_per_cta) {
   int64_t g = (rows + rows_per_cta - 1) / rows_per_cta;
   if (g < 1) g = 1;
-  if (g > RED_GRID_MAX) g = RED_GRID_MAX;
+  if (g > c->max_parts) g = c->max_parts;
   return (int)g;
 }
 

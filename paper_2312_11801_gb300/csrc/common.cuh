@@ -31,7 +31,7 @@ constexpr int JMAX = 64;         // max Lanczos basis columns (8 blocks of 8)
 constexpr int NBMAX = JMAX / KB + 1;  // basis blocks incl. the residual block
 constexpr int RMAX = 32;         // max sketch rank
 constexpr int AUG = 40;          // augmented Gram width: 36 svec + ax + w + 2 pad
-constexpr int RED_GRID_MAX = 2 * 152;
+constexpr int RED_GRID_MAX = 4 * 152;   // most CTAs of any reducing kernel
 constexpr int THREADS = 256;
 
 // ---- device-resident FP64 scalars of one instance ------------------------------------
@@ -140,7 +140,8 @@ struct Ctx {
   // scalars, Lanczos state, reductions
   DevScalars* sc = nullptr;
   DevLanczos* lz = nullptr;
-  double* partials = nullptr;   // RED_GRID_MAX x 1024
+  double* partials = nullptr;   // max_parts x PART_STRIDE
+  int max_parts = 1;            // rows of partials: the largest grid of a reducing kernel
   double* red = nullptr;        // reduced outputs (several regions)
   DevScalars* h_sc = nullptr;   // pinned host mirror
   DevLanczos* h_lz = nullptr;
@@ -253,16 +254,21 @@ template <typename T> struct Bulk {
 
 // shared-memory-staged block Gram-Schmidt kernels (orth.cu); grid = orth_grid(c, n)
 template <typename T> struct Orth {
-  static void proj(Ctx* c, const void* Qb, int nb, const void* W, const int* mask);
-  static void update(Ctx* c, const void* Qb, int nb, void* W, const int* mask);
+  // proj, update and gram_xy return the grid they launched (the partials to reduce)
+  static int proj(Ctx* c, const void* Qb, int nb, const void* W, const int* mask);
+  static int update(Ctx* c, const void* Qb, int nb, void* W, const int* mask);
   static void finalize(Ctx* c, const void* Qb, int nb, const void* W, void* out, const int* mask,
                        uint64_t seed);
   static void restart(Ctx* c, const void* Qb, int J, int nout, const double* Y, void* out,
                       const void* resid, int resid_slot);
   // X^T Y of two n x 8 blocks (partials in the layout of proj with one block)
-  static void gram_xy(Ctx* c, const void* X, const void* Y);
+  static int gram_xy(Ctx* c, const void* X, const void* Y);
 };
-int orth_grid(Ctx* c, int64_t rows);
+// CTAs of a tiled Gram-Schmidt launch: one per tile of rows, at most what stays resident
+// on every SM at once for that kernel and shared-memory size, at most max_parts
+int orth_grid(Ctx* c, int64_t rows, const void* kernel, size_t smem);
+// rows of partials a context needs: ceil(max(n, m) / 64) + 1, at most RED_GRID_MAX
+int64_t parts_needed(int64_t n, int64_t m);
 
 int red_grid(Ctx* c, int64_t rows, int rows_per_cta);
 void reduce_partials(Ctx* c, int nparts, int nvals, double* out, const int* mask = nullptr);

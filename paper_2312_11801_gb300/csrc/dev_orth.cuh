@@ -42,13 +42,17 @@ __device__ __forceinline__ void load_tile(T* stage, const T* USBS_RESTRICT Q, si
 }
 
 // ---- H = Q^T W --------------------------------------------------------------------------
-// Items (b, a-pair): 4 nb <= 32.  256 threads = 8 row groups x 32 slots; a slot owns one
-// item: 2 basis columns x all 8 columns of W (16 accumulators, 3 shared loads per 16 FMAs).
+// Items (b, a-pair): 4 nb <= 32.  256 threads = 8 row groups (warps) x 32 slots.  A slot
+// owns one item, 2 basis columns x all 8 columns of W (16 accumulators, 3 shared loads
+// per 16 FMAs).  When there are fewer items than slots, the spare slots of a warp take
+// further rows of the tile: slot = item + nitems * sub, sub < nsub = 32 / nitems, and
+// the tile's rows are dealt out over the 8 * nsub (warp, sub) pairs.  The epilogue adds
+// the partial sums in a fixed order (warp, then sub).
 template <typename T>
 __device__ __forceinline__ void accum_pair(const T* USBS_RESTRICT qcol2, const T* USBS_RESTRICT X,
-                                           int grp, T (&acc)[16]) {
+                                           int r0, int rstep, T (&acc)[16]) {
   constexpr int TR = TileRows<T>::value;
-  for (int r = grp; r < TR; r += 8) {
+  for (int r = r0; r < TR; r += rstep) {
     const T q0 = qcol2[r * 8], q1 = qcol2[r * 8 + 1];
     const T* xr = X + r * 8;
 #pragma unroll
@@ -57,6 +61,17 @@ __device__ __forceinline__ void accum_pair(const T* USBS_RESTRICT qcol2, const T
       acc[8 + c] += q1 * xr[c];
     }
   }
+}
+
+// Sum of one output t of the item layout (item = t / 16 of the [b][a][c] block order,
+// u = 16 values of a slot) over the 8 warps and the nsub row subgroups, fixed order.
+__device__ __forceinline__ double sum_slots(const double* red, int nitems, int nsub, int item,
+                                            int u, int nslot) {
+  double sum = 0.0;
+#pragma unroll
+  for (int g = 0; g < 8; ++g)
+    for (int sb = 0; sb < nsub; ++sb) sum += red[((size_t)g * nslot + item + nitems * sb) * 16 + u];
+  return sum;
 }
 
 template <typename T>
@@ -70,6 +85,9 @@ __device__ __forceinline__ void k_tproj_dev(const int cta, const int ncta, int n
   const int sstride = (nb + 1) * TR * 8;
   const int tid = threadIdx.x, grp = tid >> 5, slot = tid & 31;
   const int nitems = 4 * nb;
+  const int nsub = nitems > 0 ? 32 / nitems : 1;
+  const int item = nitems > 0 ? slot % nitems : 0, sub = nitems > 0 ? slot / nitems : 0;
+  const bool active = nitems > 0 && sub < nsub;
   T acc[16];
 #pragma unroll
   for (int u = 0; u < 16; ++u) acc[u] = (T)0;
@@ -84,29 +102,24 @@ __device__ __forceinline__ void k_tproj_dev(const int cta, const int ncta, int n
     cp_async_wait_1();
     __syncthreads();
     const T* st = stages + (it & 1) * sstride;
-    if (slot < nitems) {
-      const int b = slot >> 2, a0 = 2 * (slot & 3);
-      accum_pair<T>(st + (size_t)b * TR * 8 + a0, st + nb * TR * 8, grp, acc);
+    if (active) {
+      const int b = item >> 2, a0 = 2 * (item & 3);
+      accum_pair<T>(st + (size_t)b * TR * 8 + a0, st + nb * TR * 8, grp + 8 * sub, 8 * nsub, acc);
     }
     __syncthreads();
   }
   cp_async_wait_0();
   __syncthreads();
-  double* red = reinterpret_cast<double*>(smem_raw);     // 8 x 512
-  if (slot < nitems) {
-    const int b = slot >> 2, a0 = 2 * (slot & 3);
+  double* red = reinterpret_cast<double*>(smem_raw);     // 8 warps x 32 slots x 16
+  if (active) {
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      red[grp * 512 + b * 64 + a0 * 8 + c] = (double)acc[c];
-      red[grp * 512 + b * 64 + (a0 + 1) * 8 + c] = (double)acc[8 + c];
-    }
+    for (int u = 0; u < 16; ++u) red[((size_t)grp * 32 + slot) * 16 + u] = (double)acc[u];
   }
   __syncthreads();
   for (int t = tid; t < nb * 64; t += blockDim.x) {
-    double sum = 0.0;
-#pragma unroll
-    for (int g = 0; g < 8; ++g) sum += red[g * 512 + t];
-    partials[(size_t)cta * PART_STRIDE + t] = sum;
+    // t = b * 64 + a * 8 + c  ->  item b * 4 + a / 2, value (a % 2) * 8 + c
+    const int b = t >> 6, a = (t >> 3) & 7, c = t & 7;
+    partials[(size_t)cta * PART_STRIDE + t] = sum_slots(red, nitems, nsub, b * 4 + (a >> 1), (a & 1) * 8 + c, 32);
   }
 }
 
@@ -125,6 +138,10 @@ __device__ __forceinline__ void k_tupdate_dev(const int cta, const int ncta, int
   const int tid = threadIdx.x, grp = tid >> 5, slot = tid & 31;
   for (int t = tid; t < nb * 64; t += blockDim.x) Hs[t] = (T)Hred[t];
   const int nitems = 4 * (nb + 1);                          // item b == nb: the Gram matrix
+  // up to 32 items: one per slot, spare slots split the rows; more (nb = 8): two per slot
+  const int nsub = nitems <= 32 ? 32 / nitems : 1;
+  const int nslot = nitems <= 32 ? 32 : 64;
+  const int sub = nitems <= 32 ? slot / nitems : 0;
   T acc[2][16];
 #pragma unroll
   for (int u = 0; u < 2; ++u)
@@ -171,37 +188,34 @@ __device__ __forceinline__ void k_tupdate_dev(const int cta, const int ncta, int
     // phase 2: H2 += Q^T X and G += X^T X (rows past n are zero in X)
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
-      const int item = slot + 32 * u;
-      if (item < nitems) {
+      const int item = nitems <= 32 ? slot % nitems : slot + 32 * u;
+      const bool act = nitems <= 32 ? (u == 0 && sub < nsub) : item < nitems;
+      if (act) {
         const int b = item >> 2, a0 = 2 * (item & 3);
-        accum_pair<T>((b < nb ? st + (size_t)b * TR * 8 : Xs) + a0, Xs, grp, acc[u]);
+        accum_pair<T>((b < nb ? st + (size_t)b * TR * 8 : Xs) + a0, Xs, grp + 8 * sub, 8 * nsub, acc[u]);
       }
     }
     __syncthreads();
   }
   cp_async_wait_0();
   __syncthreads();
-  double* red = reinterpret_cast<double*>(smem_raw);     // 8 x 576
+  double* red = reinterpret_cast<double*>(smem_raw);     // 8 warps x nslot x 16
 #pragma unroll
   for (int u = 0; u < 2; ++u) {
-    const int item = slot + 32 * u;
-    if (item < nitems) {
-      const int b = item >> 2, a0 = 2 * (item & 3);
-      const int base = (b < nb ? b * 64 : 512) + a0 * 8;
+    const bool act = nitems <= 32 ? (u == 0 && sub < nsub) : slot + 32 * u < nitems;
+    if (act) {
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        red[grp * 576 + base + c] = (double)acc[u][c];
-        red[grp * 576 + base + 8 + c] = (double)acc[u][8 + c];
-      }
+      for (int v = 0; v < 16; ++v) red[((size_t)grp * nslot + slot + 32 * u) * 16 + v] = (double)acc[u][v];
     }
   }
   __syncthreads();
   for (int t = tid; t < 576; t += blockDim.x) {
     if (t < 512 && t >= nb * 64) continue;
-    double sum = 0.0;
-#pragma unroll
-    for (int g = 0; g < 8; ++g) sum += red[g * 576 + t];
-    partials[(size_t)cta * PART_STRIDE + t] = sum;
+    // t < 512: H2 block b = t / 64; t >= 512: the Gram matrix, item block nb
+    const int b = t < 512 ? (t >> 6) : nb, a = (t >> 3) & 7, c = t & 7;
+    partials[(size_t)cta * PART_STRIDE + t] =
+        sum_slots(red, nitems <= 32 ? nitems : 0, nitems <= 32 ? nsub : 1, b * 4 + (a >> 1),
+                  (a & 1) * 8 + c, nslot);
   }
 }
 
@@ -312,8 +326,13 @@ __device__ __forceinline__ void k_trestart_dev(const int cta, const int ncta, in
     cp_async_wait_1();
     __syncthreads();
     const T* st = stages + (it & 1) * sstride;
-    for (int p = tid; p < (TR / 2) * nout; p += blockDim.x) {
-      const int r0 = 2 * (p / nout), o = p % nout;
+    // items (row pair, output block, column group): with nout < 4 the 8 columns of an
+    // output block are split into 4 / nout groups so that every thread has work
+    const int ngrp = nout >= 4 ? 1 : 4 / nout, ncols = 8 / ngrp;
+    for (int p = tid; p < (TR / 2) * nout * ngrp; p += blockDim.x) {
+      const int pair = p / (nout * ngrp), rem = p % (nout * ngrp);
+      const int o = rem / ngrp, c0 = (rem % ngrp) * ncols;
+      const int r0 = 2 * pair;
       T acc0[8], acc1[8];
 #pragma unroll
       for (int v = 0; v < 8; ++v) { acc0[v] = (T)0; acc1[v] = (T)0; }
@@ -323,22 +342,26 @@ __device__ __forceinline__ void k_trestart_dev(const int cta, const int ncta, in
 #pragma unroll
         for (int a = 0; a < 8; ++a) {
           const T q0 = qr0[a], q1 = qr1[a];
-          const T* yr = Ys + (b * 8 + a) * ncol + 8 * o;
+          const T* yr = Ys + (b * 8 + a) * ncol + 8 * o + c0;
 #pragma unroll
           for (int v = 0; v < 8; ++v) {
-            acc0[v] += q0 * yr[v];
-            acc1[v] += q1 * yr[v];
+            if (v < ncols) {
+              acc0[v] += q0 * yr[v];
+              acc1[v] += q1 * yr[v];
+            }
           }
         }
       }
       const int row0 = tile * TR + r0;
       if (row0 < n) {
 #pragma unroll
-        for (int v = 0; v < 8; ++v) out[o * ostride + (size_t)8 * row0 + v] = acc0[v];
+        for (int v = 0; v < 8; ++v)
+          if (v < ncols) out[o * ostride + (size_t)8 * row0 + c0 + v] = acc0[v];
       }
       if (row0 + 1 < n) {
 #pragma unroll
-        for (int v = 0; v < 8; ++v) out[o * ostride + (size_t)8 * (row0 + 1) + v] = acc1[v];
+        for (int v = 0; v < 8; ++v)
+          if (v < ncols) out[o * ostride + (size_t)8 * (row0 + 1) + c0 + v] = acc1[v];
       }
     }
     if (resid) {

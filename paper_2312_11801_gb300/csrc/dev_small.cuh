@@ -313,6 +313,111 @@ __device__ __forceinline__ void k_chol_block_dev(DevLanczos* lz, const double* U
   }
 }
 
+// ---- Jacobi sweeps of a 32 x 32 matrix on one warp, in registers (FP32) ----------------------
+// Lane l keeps row l of A and row l of the rotation product V.  The index pairs of a round
+// are the positions (2k, 2k + 1); after the round, rows and columns of A and the columns
+// of V move by a fixed permutation of positions (the round-robin rotation that keeps
+// slot 0 and turns slots 1..31, with slot i at position 2i and slot 31 - i at 2i + 1), so
+// every index pair shares a rotation once every 31 rounds.  Row moves are shuffles;
+// column moves are compile-time renamings of registers.  Work stays in position space:
+// the diagonal and the columns of V that come back are the eigenvalues and the matching
+// eigenvectors.
+__host__ __device__ constexpr int jw_slot_of_pos(int x) { return (x & 1) ? 31 - (x >> 1) : (x >> 1); }
+__host__ __device__ constexpr int jw_pos_of_slot(int i) { return i <= 15 ? 2 * i : 2 * (31 - i) + 1; }
+__host__ __device__ constexpr int jw_prev_slot(int i) { return i == 0 ? 0 : (i == 1 ? 31 : i - 1); }
+__host__ __device__ constexpr int jw_perm(int x) { return jw_pos_of_slot(jw_prev_slot(jw_slot_of_pos(x))); }
+
+// A and V in shared memory, row stride ld; V is overwritten (it starts as the identity).
+// Returns the number of sweeps taken.  Stops when the off-diagonal Frobenius norm is at
+// most eps times the whole norm, or after max_sweeps.
+__device__ __forceinline__ int jacobi_warp32(float* A, float* Vm, int ld, int max_sweeps, float eps,
+                                             float skip) {
+  const int lane = threadIdx.x & 31;
+  const bool even = (lane & 1) == 0;
+  const int src = jw_perm(lane);
+  float a[32], v[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) {
+    a[c] = A[lane * ld + c];
+    v[c] = (c == lane) ? 1.f : 0.f;
+  }
+  float dg = A[lane * ld + lane];
+  int sweeps = 0;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    double tot = 0.0, dd = 0.0;
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+      tot += (double)a[c] * (double)a[c];
+      if (c == lane) dd = (double)a[c] * (double)a[c];
+    }
+    double off = tot - dd;
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(FULL, off, o);
+      tot += __shfl_xor_sync(FULL, tot, o);
+    }
+    if (off <= (double)eps * (double)eps * tot) break;
+    ++sweeps;
+    for (int round = 0; round < 31; ++round) {
+      // rotation of the pair (2k, 2k + 1) = (lane & ~1, lane | 1), from the even lane's A[p][q]
+      float apq_own = 0.f;
+#pragma unroll
+      for (int c = 0; c < 32; ++c) apq_own = (c == (lane ^ 1)) ? a[c] : apq_own;
+      const float apq = __shfl_sync(FULL, apq_own, lane & ~1);
+      const float dpart = __shfl_xor_sync(FULL, dg, 1);
+      const float app = even ? dg : dpart, aqq = even ? dpart : dg;
+      float cs = 1.f, sn = 0.f;
+      if (apq != 0.f && fabsf(apq) > skip * sqrtf(fabsf(app * aqq))) {
+        const float tau = (aqq - app) / (2.f * apq);
+        float t;
+        if (fabsf(tau) > 1e18f) t = 0.5f / tau;
+        else t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(tau * tau + 1.f));
+        cs = 1.f / sqrtf(t * t + 1.f);
+        sn = t * cs;
+      }
+      // rows: [p; q] <- [c -s; s c] [p; q]
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        const float o = __shfl_xor_sync(FULL, a[c], 1);
+        a[c] = even ? (cs * a[c] - sn * o) : (sn * o + cs * a[c]);
+      }
+      // columns of A and V: [p q] <- [p q] [c s; -s c], every pair with its own rotation
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const float ck = __shfl_sync(FULL, cs, 2 * k), sk = __shfl_sync(FULL, sn, 2 * k);
+        float x = a[2 * k], y = a[2 * k + 1];
+        a[2 * k] = ck * x - sk * y;
+        a[2 * k + 1] = sk * x + ck * y;
+        x = v[2 * k];
+        y = v[2 * k + 1];
+        v[2 * k] = ck * x - sk * y;
+        v[2 * k + 1] = sk * x + ck * y;
+      }
+      dg = even ? (cs * cs * app - 2.f * cs * sn * apq + sn * sn * aqq)
+                : (sn * sn * app + 2.f * cs * sn * apq + cs * cs * aqq);
+      // move to the next round's positions: rows across lanes, columns within registers
+#pragma unroll
+      for (int c = 0; c < 32; ++c) a[c] = __shfl_sync(FULL, a[c], src);
+      dg = __shfl_sync(FULL, dg, src);
+      float t[32];
+#pragma unroll
+      for (int x = 0; x < 32; ++x) t[x] = a[jw_perm(x)];
+#pragma unroll
+      for (int x = 0; x < 32; ++x) a[x] = t[x];
+#pragma unroll
+      for (int x = 0; x < 32; ++x) t[x] = v[jw_perm(x)];
+#pragma unroll
+      for (int x = 0; x < 32; ++x) v[x] = t[x];
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 32; ++c) {
+    A[lane * ld + c] = a[c];
+    Vm[lane * ld + c] = v[c];
+  }
+  __syncwarp();
+  return sweeps;
+}
+
 // ---- Rayleigh-Ritz: eigen-decomposition of T by parallel cyclic Jacobi ------------------------
 // S is the arithmetic of the whole Ritz step (FP32 in mixed mode, where GB300's FP64 rate
 // would make this one CTA the bottleneck; FP64 in the plain mode).  The J/2 rotations
@@ -366,82 +471,93 @@ __device__ __forceinline__ void k_ritz_dev(DevLanczos* lz, int kc, double tol, i
     return;
   }
   const S skip = (S)(jac_eps * 1e-2), big = (S)1e18;
-  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    double off = 0.0, tot = 0.0;
-    for (int t = tid; t < J * J; t += blockDim.x) {
-      const int i = t / J, j = t % J;
-      const double x = (double)A[i * LD + j];
-      tot += x * x;
-      if (i != j) off += x * x;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      off += __shfl_xor_sync(0xffffffffu, off, o);
-      tot += __shfl_xor_sync(0xffffffffu, tot, o);
-    }
-    if (lane == 0) { wred[0][warp] = off; wred[1][warp] = tot; }
-    __syncthreads();
-    if (tid == 0) {
-      double o2 = 0.0, t2 = 0.0;
-      for (int w = 0; w < nw; ++w) { o2 += wred[0][w]; t2 += wred[1][w]; }
-      stop = (o2 <= jac_eps * jac_eps * t2) ? 1 : 0;
+  if constexpr (J == 32 && sizeof(S) == 4) {
+    // one warp, registers only (the other warps wait at the barrier)
+    (void)big;
+    if (warp == 0) {
+      const int sw = jacobi_warp32(reinterpret_cast<float*>(A), reinterpret_cast<float*>(Vv), LD,
+                                   max_sweeps, (float)jac_eps, (float)skip);
+      if (lane == 0) lz->sweeps += sw;
     }
     __syncthreads();
-    if (stop) break;
-    if (tid == 0) lz->sweeps += 1;
-    for (int round = 0; round < J - 1; ++round) {
-      if (tid < half) {
-        // circle method: position 0 fixed, the others rotate
-        const int k = tid;
-        const int posA = k, posB = J - 1 - k;
-        const int pa = posA == 0 ? 0 : 1 + ((posA - 1 + round) % (J - 1));
-        const int pb = 1 + ((posB - 1 + round) % (J - 1));
-        const int p = min(pa, pb), q = max(pa, pb);
-        pp[k] = p;
-        qq[k] = q;
-        const S apq = A[p * LD + q];
-        S c = (S)1, sv = (S)0;
-        const S app = A[p * LD + p], aqq = A[q * LD + q];
-        // all in S: an FP64 sqrt here would be a long FP64 sequence every round
-        if (apq != (S)0 && fabs(apq) > skip * sqrt(fabs(app * aqq))) {
-          const S tau = (aqq - app) / ((S)2 * apq);
-          S t;
-          if (fabs(tau) > big) t = (S)0.5 / tau;
-          else t = (tau >= (S)0 ? (S)1 : (S)-1) / (fabs(tau) + sqrt(tau * tau + (S)1));
-          c = (S)1 / sqrt(t * t + (S)1);
-          sv = t * c;
-        }
-        cs[k] = c;
-        sn[k] = sv;
+  } else {
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+      double off = 0.0, tot = 0.0;
+      for (int t = tid; t < J * J; t += blockDim.x) {
+        const int i = t / J, j = t % J;
+        const double x = (double)A[i * LD + j];
+        tot += x * x;
+        if (i != j) off += x * x;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        off += __shfl_xor_sync(0xffffffffu, off, o);
+        tot += __shfl_xor_sync(0xffffffffu, tot, o);
+      }
+      if (lane == 0) { wred[0][warp] = off; wred[1][warp] = tot; }
+      __syncthreads();
+      if (tid == 0) {
+        double o2 = 0.0, t2 = 0.0;
+        for (int w = 0; w < nw; ++w) { o2 += wred[0][w]; t2 += wred[1][w]; }
+        stop = (o2 <= jac_eps * jac_eps * t2) ? 1 : 0;
       }
       __syncthreads();
-      // A <- G^T A G on 2 x 2 blocks; V <- V G (index arithmetic on powers of two)
-      constexpr int NBLK = half * half, NITEM = half * half + J * half;
-      for (int t = tid; t < NITEM; t += blockDim.x) {
-        if (t < NBLK) {
-          const int k1 = t / half, k2 = t % half;
-          const int p1 = pp[k1], q1 = qq[k1], p2 = pp[k2], q2 = qq[k2];
-          const S c1 = cs[k1], s1 = sn[k1], c2 = cs[k2], s2 = sn[k2];
-          const S a = A[p1 * LD + p2], b = A[p1 * LD + q2];
-          const S cc = A[q1 * LD + p2], d = A[q1 * LD + q2];
-          // rows: [p1; q1] <- [c1 -s1; s1 c1] [p1; q1]
-          const S ra = c1 * a - s1 * cc, rb = c1 * b - s1 * d;
-          const S rc = s1 * a + c1 * cc, rd = s1 * b + c1 * d;
-          // cols: [p2 q2] <- [p2 q2] [c2 s2; -s2 c2]
-          A[p1 * LD + p2] = c2 * ra - s2 * rb;
-          A[p1 * LD + q2] = s2 * ra + c2 * rb;
-          A[q1 * LD + p2] = c2 * rc - s2 * rd;
-          A[q1 * LD + q2] = s2 * rc + c2 * rd;
-        } else {
-          const int u = t - NBLK;
-          const int k = u / J, row = u % J;
-          const S c = cs[k], sv = sn[k];
-          const int p = pp[k], q = qq[k];
-          const S vp = Vv[row * LD + p], vq = Vv[row * LD + q];
-          Vv[row * LD + p] = c * vp - sv * vq;
-          Vv[row * LD + q] = sv * vp + c * vq;
+      if (stop) break;
+      if (tid == 0) lz->sweeps += 1;
+      for (int round = 0; round < J - 1; ++round) {
+        if (tid < half) {
+          // circle method: position 0 fixed, the others rotate
+          const int k = tid;
+          const int posA = k, posB = J - 1 - k;
+          const int pa = posA == 0 ? 0 : 1 + ((posA - 1 + round) % (J - 1));
+          const int pb = 1 + ((posB - 1 + round) % (J - 1));
+          const int p = min(pa, pb), q = max(pa, pb);
+          pp[k] = p;
+          qq[k] = q;
+          const S apq = A[p * LD + q];
+          S c = (S)1, sv = (S)0;
+          const S app = A[p * LD + p], aqq = A[q * LD + q];
+          // all in S: an FP64 sqrt here would be a long FP64 sequence every round
+          if (apq != (S)0 && fabs(apq) > skip * sqrt(fabs(app * aqq))) {
+            const S tau = (aqq - app) / ((S)2 * apq);
+            S t;
+            if (fabs(tau) > big) t = (S)0.5 / tau;
+            else t = (tau >= (S)0 ? (S)1 : (S)-1) / (fabs(tau) + sqrt(tau * tau + (S)1));
+            c = (S)1 / sqrt(t * t + (S)1);
+            sv = t * c;
+          }
+          cs[k] = c;
+          sn[k] = sv;
         }
+        __syncthreads();
+        // A <- G^T A G on 2 x 2 blocks; V <- V G (index arithmetic on powers of two)
+        constexpr int NBLK = half * half, NITEM = half * half + J * half;
+        for (int t = tid; t < NITEM; t += blockDim.x) {
+          if (t < NBLK) {
+            const int k1 = t / half, k2 = t % half;
+            const int p1 = pp[k1], q1 = qq[k1], p2 = pp[k2], q2 = qq[k2];
+            const S c1 = cs[k1], s1 = sn[k1], c2 = cs[k2], s2 = sn[k2];
+            const S a = A[p1 * LD + p2], b = A[p1 * LD + q2];
+            const S cc = A[q1 * LD + p2], d = A[q1 * LD + q2];
+            // rows: [p1; q1] <- [c1 -s1; s1 c1] [p1; q1]
+            const S ra = c1 * a - s1 * cc, rb = c1 * b - s1 * d;
+            const S rc = s1 * a + c1 * cc, rd = s1 * b + c1 * d;
+            // cols: [p2 q2] <- [p2 q2] [c2 s2; -s2 c2]
+            A[p1 * LD + p2] = c2 * ra - s2 * rb;
+            A[p1 * LD + q2] = s2 * ra + c2 * rb;
+            A[q1 * LD + p2] = c2 * rc - s2 * rd;
+            A[q1 * LD + q2] = s2 * rc + c2 * rd;
+          } else {
+            const int u = t - NBLK;
+            const int k = u / J, row = u % J;
+            const S c = cs[k], sv = sn[k];
+            const int p = pp[k], q = qq[k];
+            const S vp = Vv[row * LD + p], vq = Vv[row * LD + q];
+            Vv[row * LD + p] = c * vp - sv * vq;
+            Vv[row * LD + q] = sv * vp + c * vq;
+          }
+        }
+        __syncthreads();
       }
-      __syncthreads();
     }
   }
   // descending order under a strict total order (value, then index)

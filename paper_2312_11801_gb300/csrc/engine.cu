@@ -376,9 +376,10 @@ static int build_ctx(Ctx* c, const HostProblem& hp, const float* Psi) {
   USBS_TRY(dalloc(c, &c->lz, 1));
   USBS_CUDA_TRY(c, cudaMemsetAsync(c->sc, 0, sizeof(DevScalars), c->stream));
   USBS_CUDA_TRY(c, cudaMemsetAsync(c->lz, 0, sizeof(DevLanczos), c->stream));
-  USBS_TRY(dalloc(c, &c->partials, (size_t)RED_GRID_MAX * PART_STRIDE));
+  c->max_parts = (int)parts_needed(n, m);
+  USBS_TRY(dalloc(c, &c->partials, (size_t)c->max_parts * PART_STRIDE));
   USBS_TRY(dalloc(c, &c->red, (size_t)RED_TOTAL));
-  USBS_CUDA_TRY(c, cudaMemsetAsync(c->partials, 0, sizeof(double) * RED_GRID_MAX * PART_STRIDE, c->stream));
+  USBS_CUDA_TRY(c, cudaMemsetAsync(c->partials, 0, sizeof(double) * c->max_parts * PART_STRIDE, c->stream));
   USBS_CUDA_TRY(c, cudaMemsetAsync(c->red, 0, sizeof(double) * RED_TOTAL, c->stream));
   USBS_CUDA_TRY(c, cudaMallocHost(reinterpret_cast<void**>(&c->h_sc), sizeof(DevScalars)));
   USBS_CUDA_TRY(c, cudaMallocHost(reinterpret_cast<void**>(&c->h_lz), sizeof(DevLanczos)));
@@ -472,14 +473,15 @@ static int init_cuda(Ctx* c) {
 // ---------------------------------------------------------------------------------------
 template <typename T>
 static void orth_block(Ctx* c, T* Q, int nb, T* W, T* out, int j, int write_T, int is_resid) {
-  const int np = orth_grid(c, c->n);
   const int* defl = DEV_FIELD(c->lz, DevLanczos, defl, int);
   if (nb > 0) {
-    Orth<T>::proj(c, Q, nb, W, nullptr);
+    const int np = Orth<T>::proj(c, Q, nb, W, nullptr);
     reduce_partials(c, np, nb * 64, c->red + RED_H);
   }
-  Orth<T>::update(c, Q, nb, W, nullptr);
-  reduce_partials(c, np, 576, c->red + RED_H2);
+  {
+    const int np = Orth<T>::update(c, Q, nb, W, nullptr);
+    reduce_partials(c, np, 576, c->red + RED_H2);
+  }
   launch_chol_block(c, j, nb, write_T, is_resid, 0);
   Orth<T>::finalize(c, Q, nb, W, out, nullptr, c->seed + 0x1000003ull * (c->rng_counter++));
   // masked second and third passes: only run when a column was replaced by a random
@@ -488,10 +490,10 @@ static void orth_block(Ctx* c, T* Q, int nb, T* W, T* out, int j, int write_T, i
   for (int pass = 1; pass <= 2; ++pass) {
     const int* mask = pass == 1 ? defl : defl2;
     if (nb > 0) {
-      Orth<T>::proj(c, Q, nb, out, mask);
+      const int np = Orth<T>::proj(c, Q, nb, out, mask);
       reduce_partials(c, np, nb * 64, c->red + RED_H, mask);
     }
-    Orth<T>::update(c, Q, nb, out, mask);
+    const int np = Orth<T>::update(c, Q, nb, out, mask);
     reduce_partials(c, np, 576, c->red + RED_H2, mask);
     launch_chol_block(c, j, nb, 0, is_resid, pass);
     Orth<T>::finalize(c, Q, nb, out, out, mask, c->seed + 0x2000011ull * (c->rng_counter++));
@@ -634,8 +636,7 @@ static int step_impl(Ctx* c, usbs_step_info* info) {
   const int npg = red_grid(c, c->m, 128);
   // V^T C V
   Bulk<T>::spmm(c, c->valC, c->dC, c->V, c->W);
-  Orth<T>::gram_xy(c, c->V, c->W);
-  reduce_partials(c, orth_grid(c, c->n), 64, c->red + RED_VC);
+  reduce_partials(c, Orth<T>::gram_xy(c, c->V, c->W), 64, c->red + RED_VC);
   // [G | A Xbar | y - b/rho]^T [G | A Xbar | y - b/rho]
   Bulk<T>::gstats(c, c->V, c->ax, c->y, npg);
   reduce_partials(c, npg, 880, c->red + RED_AUG);

@@ -12,6 +12,7 @@
 // ([b*64 + a*8 + c] for H_b[a][c]; [512 + a*8 + c] for the Gram matrix).
 #include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "common.cuh"
 #include "dev_orth.cuh"
@@ -70,40 +71,71 @@ void set_attrs() {
 
 }  // namespace
 
-int orth_grid(Ctx* c, int64_t rows) {
+int64_t parts_needed(int64_t n, int64_t m) {
+  const int64_t g = (std::max(n, m) + 63) / 64 + 1;
+  return std::min<int64_t>(g, RED_GRID_MAX);
+}
+
+// resident CTAs per SM of a kernel at a dynamic shared-memory size, cached (one device)
+static int resident_ctas(const void* kernel, size_t smem) {
+  struct Entry { const void* k; size_t s; int v; };
+  static std::mutex mu;
+  static std::vector<Entry> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  for (const Entry& e : cache)
+    if (e.k == kernel && e.s == smem) return e.v;
+  int v = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, 256, smem) != cudaSuccess) {
+    cudaGetLastError();
+    v = 1;
+  }
+  v = std::max(v, 1);
+  cache.push_back({kernel, smem, v});
+  return v;
+}
+
+int orth_grid(Ctx* c, int64_t rows, const void* kernel, size_t smem) {
   const int TR = c->fp64 ? TileRows<double>::value : TileRows<float>::value;
   int64_t g = (rows + TR - 1) / TR;
-  const int64_t cap = std::min<int64_t>(RED_GRID_MAX, 2 * (int64_t)c->num_sms);
+  const int64_t cap = std::min<int64_t>(c->max_parts, (int64_t)resident_ctas(kernel, smem) * c->num_sms);
   if (g > cap) g = cap;
   return (int)(g < 1 ? 1 : g);
 }
 
 template <typename T>
-void Orth<T>::proj(Ctx* c, const void* Qb, int nb, const void* W, const int* mask) {
+int Orth<T>::proj(Ctx* c, const void* Qb, int nb, const void* W, const int* mask) {
   USBS_LAUNCH_B(c, USBS_KIND_REORTH, mask ? 0.0 : 8.0 * sizeof(T) * c->n * (nb + 1));
   set_attrs<T>();
-  // the epilogue reuses the stage buffers for 4 x 512 FP64 partial sums
+  // the epilogue reuses the stage buffers for 8 x 32 x 16 FP64 partial sums
   const size_t sm = std::max(tile_smem<T>(nb, 0), sizeof(double) * 8 * 512);
-  k_tproj<T><<<orth_grid(c, c->n), 256, sm, c->stream>>>((int)c->n, (const T*)Qb, (size_t)c->n * 8,
-                                                         nb, (const T*)W, c->partials, mask);
+  const int g = orth_grid(c, c->n, (const void*)k_tproj<T>, sm);
+  k_tproj<T><<<g, 256, sm, c->stream>>>((int)c->n, (const T*)Qb, (size_t)c->n * 8, nb, (const T*)W,
+                                        c->partials, mask);
+  return g;
 }
 
 template <typename T>
-void Orth<T>::gram_xy(Ctx* c, const void* X, const void* Y) {
+int Orth<T>::gram_xy(Ctx* c, const void* X, const void* Y) {
   USBS_LAUNCH_B(c, USBS_KIND_REORTH, 16.0 * sizeof(T) * c->n);
   set_attrs<T>();
   const size_t sm = std::max(tile_smem<T>(1, 0), sizeof(double) * 8 * 512);
-  k_tproj<T><<<orth_grid(c, c->n), 256, sm, c->stream>>>((int)c->n, (const T*)X, (size_t)c->n * 8,
-                                                         1, (const T*)Y, c->partials, nullptr);
+  const int g = orth_grid(c, c->n, (const void*)k_tproj<T>, sm);
+  k_tproj<T><<<g, 256, sm, c->stream>>>((int)c->n, (const T*)X, (size_t)c->n * 8, 1, (const T*)Y,
+                                        c->partials, nullptr);
+  return g;
 }
 
 template <typename T>
-void Orth<T>::update(Ctx* c, const void* Qb, int nb, void* W, const int* mask) {
+int Orth<T>::update(Ctx* c, const void* Qb, int nb, void* W, const int* mask) {
   USBS_LAUNCH_B(c, USBS_KIND_REORTH_UPDATE, mask ? 0.0 : 8.0 * sizeof(T) * c->n * (nb + 2));
   set_attrs<T>();
-  const size_t sm = std::max(tile_smem<T>(nb, 8 * 64), sizeof(double) * 8 * 576);
-  k_tupdate<T><<<orth_grid(c, c->n), 256, sm, c->stream>>>((int)c->n, (const T*)Qb, (size_t)c->n * 8,
-                                                           nb, (T*)W, c->red + RED_H, c->partials, mask);
+  // the epilogue reuses the stage buffers for 8 x (32 or 64) x 16 FP64 partial sums
+  const size_t sm = std::max(tile_smem<T>(nb, 8 * 64),
+                             sizeof(double) * 8 * (4 * (nb + 1) <= 32 ? 32 : 64) * 16);
+  const int g = orth_grid(c, c->n, (const void*)k_tupdate<T>, sm);
+  k_tupdate<T><<<g, 256, sm, c->stream>>>((int)c->n, (const T*)Qb, (size_t)c->n * 8, nb, (T*)W,
+                                          c->red + RED_H, c->partials, mask);
+  return g;
 }
 
 template <typename T>
@@ -112,7 +144,7 @@ void Orth<T>::finalize(Ctx* c, const void* Qb, int nb, const void* W, void* out,
   USBS_LAUNCH_B(c, USBS_KIND_REORTH_FINAL, mask ? 0.0 : 8.0 * sizeof(T) * c->n * (nb + 2));
   set_attrs<T>();
   const size_t sm = tile_smem<T>(nb, 8 * 64 + 64);
-  k_tfinalize<T><<<orth_grid(c, c->n), 256, sm, c->stream>>>(
+  k_tfinalize<T><<<orth_grid(c, c->n, (const void*)k_tfinalize<T>, sm), 256, sm, c->stream>>>(
       (int)c->n, (const T*)Qb, (size_t)c->n * 8, nb, (const T*)W, c->red + RED_H2, c->lz, (T*)out,
       mask, seed);
 }
@@ -123,7 +155,7 @@ void Orth<T>::restart(Ctx* c, const void* Qb, int J, int nout, const double* Y, 
   USBS_LAUNCH_B(c, USBS_KIND_RESTART, 8.0 * sizeof(T) * c->n * (J / 8 + nout + (resid ? 2 : 0)));
   set_attrs<T>();
   const size_t sm = sizeof(T) * (2 * (size_t)(J / 8) * TileRows<T>::value * 8 + (size_t)J * nout * 8);
-  k_trestart<T><<<orth_grid(c, c->n), 256, sm, c->stream>>>(
+  k_trestart<T><<<orth_grid(c, c->n, (const void*)k_trestart<T>, sm), 256, sm, c->stream>>>(
       (int)c->n, (const T*)Qb, (size_t)c->n * 8, J / 8, nout, Y, (T*)out, (size_t)c->n * 8,
       (const T*)resid, resid_slot);
 }

@@ -228,7 +228,8 @@ static uint64_t instance_bytes(int64_t n, int64_t nnz_off, int64_t m, int64_t nn
   b += 6.0 * 8.0 * m;                                                           // y, y~, AXbar, AX, nu, tmp
   b += es * 8.0 * n * (3 + 2 * NBMAX);                                          // V, V_new, W, Q, Q2
   b += 8.0 * n * r;                                                             // P, Psi
-  b += 8.0 * (RED_GRID_MAX * PART_STRIDE + RED_TOTAL) + 2.0 * (sizeof(DevScalars) + sizeof(DevLanczos));
+  b += 8.0 * ((double)parts_needed(n, m) * PART_STRIDE + RED_TOTAL) +
+       2.0 * (sizeof(DevScalars) + sizeof(DevLanczos));
   return (uint64_t)(b * 1.02 + (1 << 20));                                      // + allocation slack
 }
 
