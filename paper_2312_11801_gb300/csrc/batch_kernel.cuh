@@ -183,8 +183,7 @@ __device__ int b_step(BatchCtx<T>& b, T*& V, T*& Vnew, double*& ax, double*& axn
   __syncthreads();
   int n_alt;
   for (n_alt = 1; n_alt <= d->max_alt; ++n_alt) {
-    if (threadIdx.x < 32)
-      k_ipm_dev(sc, red, d->kc, d->alpha, d->rho, d->ipm_mu_tol, d->ipm_max_iter, n_alt == 1);
+    k_ipm_dev(sc, red, d->kc, d->alpha, d->rho, d->ipm_mu_tol, d->ipm_max_iter, n_alt == 1);
     __syncthreads();
     if (!d->any_ineq) break;
     k_alt_dev<T>(0, 1, m, d->con_ptr, d->ent_i, d->ent_j, (const T*)d->ent_v, V, sc, ax, d->y,
@@ -274,9 +273,9 @@ size_t batch_smem(int J) {
   constexpr int TR = sizeof(T) == 8 ? 64 : 128;
   const int nbmax = J / 8;   // projections run against at most J/8 blocks
   size_t m = 0;
-  m = std::max(m, sizeof(T) * (2 * (size_t)(nbmax + 1) * TR * 8 + 8 * 64 + 64));  // tiles
+  m = std::max(m, sizeof(T) * (2 * (size_t)(nbmax + 1) * BlockStride<T>::value + 8 * 64 + 64));  // tiles
   m = std::max(m, sizeof(double) * 8 * 576);                                      // epilogues
-  m = std::max(m, sizeof(T) * (2 * (size_t)nbmax * TR * 8 + (size_t)J * (J / 2)));  // restart
+  m = std::max(m, sizeof(T) * (2 * (size_t)nbmax * BlockStride<T>::value + (size_t)J * (J / 2)));  // restart
   m = std::max(m, sizeof(T) * (4 * (size_t)J * (J + 1) + (size_t)J * J / 2));       // Ritz
   m = std::max(m, sizeof(T) * 128 * AUG + sizeof(double) * 4 * 880);              // gstats
   return m;

@@ -12,6 +12,47 @@ namespace {
 template <typename T> struct TileRows;
 template <> struct TileRows<float> { static constexpr int value = 128; };
 template <> struct TileRows<double> { static constexpr int value = 64; };
+// a staged block is TR rows of 8 values plus 32 bytes: the same row of consecutive blocks
+// then falls in different shared-memory banks (TR * 8 values alone is a multiple of 128 B)
+template <typename T> struct BlockStride {
+  static constexpr int value = TileRows<T>::value * 8 + 32 / (int)sizeof(T);
+};
+
+// vector shared-memory accesses: 4 or 8 consecutive values (16-byte aligned), 2 values
+// (8-byte aligned for float, 16-byte for double)
+template <typename T> __device__ __forceinline__ void lds4(const T* p, T (&v)[4]);
+template <> __device__ __forceinline__ void lds4<float>(const float* p, float (&v)[4]) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+}
+template <> __device__ __forceinline__ void lds4<double>(const double* p, double (&v)[4]) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+template <typename T> __device__ __forceinline__ void lds8(const T* p, T (&v)[8]) {
+  T a[4], b[4];
+  lds4<T>(p, a);
+  lds4<T>(p + 4, b);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) { v[u] = a[u]; v[4 + u] = b[u]; }
+}
+template <typename T> __device__ __forceinline__ void lds2(const T* p, T& x, T& y);
+template <> __device__ __forceinline__ void lds2<float>(const float* p, float& x, float& y) {
+  const float2 a = *reinterpret_cast<const float2*>(p);
+  x = a.x; y = a.y;
+}
+template <> __device__ __forceinline__ void lds2<double>(const double* p, double& x, double& y) {
+  const double2 a = *reinterpret_cast<const double2*>(p);
+  x = a.x; y = a.y;
+}
+template <typename T> __device__ __forceinline__ void sts4(T* p, const T (&v)[4]);
+template <> __device__ __forceinline__ void sts4<float>(float* p, const float (&v)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+template <> __device__ __forceinline__ void sts4<double>(double* p, const double (&v)[4]) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
   const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
@@ -23,7 +64,7 @@ __device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_
 __device__ __forceinline__ void cp_async_wait_0() { asm volatile("cp.async.wait_group 0;\n" ::); }
 
 // Copy rows [row0, row0 + TR) of blocks 0..nq-1 of Q (and of W if W != nullptr, placed
-// after them) into one stage: layout stage[blk][r][8].
+// after them) into one stage: block blk at blk * BlockStride, row r at r * 8 within it.
 template <typename T, int TR>
 __device__ __forceinline__ void load_tile(T* stage, const T* USBS_RESTRICT Q, size_t bstride, int nq,
                                           const T* USBS_RESTRICT W, int n, int row0) {
@@ -37,7 +78,7 @@ __device__ __forceinline__ void load_tile(T* stage, const T* USBS_RESTRICT Q, si
     const int row = row0 + r;
     const bool valid = row < n;
     const T* src = (b < nq ? Q + b * bstride : W) + (size_t)8 * (valid ? row : 0) + ch * (16 / sizeof(T));
-    cp_async16(stage + ((size_t)b * TR + r) * 8 + ch * (16 / sizeof(T)), src, valid);
+    cp_async16(stage + (size_t)b * BlockStride<T>::value + (size_t)r * 8 + ch * (16 / sizeof(T)), src, valid);
   }
 }
 
@@ -53,8 +94,9 @@ __device__ __forceinline__ void accum_pair(const T* USBS_RESTRICT qcol2, const T
                                            int r0, int rstep, T (&acc)[16]) {
   constexpr int TR = TileRows<T>::value;
   for (int r = r0; r < TR; r += rstep) {
-    const T q0 = qcol2[r * 8], q1 = qcol2[r * 8 + 1];
-    const T* xr = X + r * 8;
+    T q0, q1, xr[8];
+    lds2<T>(qcol2 + r * 8, q0, q1);
+    lds8<T>(X + r * 8, xr);
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       acc[c] += q0 * xr[c];
@@ -82,7 +124,7 @@ __device__ __forceinline__ void k_tproj_dev(const int cta, const int ncta, int n
   constexpr int TR = TileRows<T>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* stages = reinterpret_cast<T*>(smem_raw);
-  const int sstride = (nb + 1) * TR * 8;
+  const int sstride = (nb + 1) * BlockStride<T>::value;
   const int tid = threadIdx.x, grp = tid >> 5, slot = tid & 31;
   const int nitems = 4 * nb;
   const int nsub = nitems > 0 ? 32 / nitems : 1;
@@ -104,7 +146,7 @@ __device__ __forceinline__ void k_tproj_dev(const int cta, const int ncta, int n
     const T* st = stages + (it & 1) * sstride;
     if (active) {
       const int b = item >> 2, a0 = 2 * (item & 3);
-      accum_pair<T>(st + (size_t)b * TR * 8 + a0, st + nb * TR * 8, grp + 8 * sub, 8 * nsub, acc);
+      accum_pair<T>(st + (size_t)b * BlockStride<T>::value + a0, st + (size_t)nb * BlockStride<T>::value, grp + 8 * sub, 8 * nsub, acc);
     }
     __syncthreads();
   }
@@ -133,7 +175,7 @@ __device__ __forceinline__ void k_tupdate_dev(const int cta, const int ncta, int
   constexpr int TR = TileRows<T>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* stages = reinterpret_cast<T*>(smem_raw);
-  const int sstride = (nb + 1) * TR * 8;
+  const int sstride = (nb + 1) * BlockStride<T>::value;
   T* Hs = stages + 2 * sstride;                             // nb x 8 x 8
   const int tid = threadIdx.x, grp = tid >> 5, slot = tid & 31;
   for (int t = tid; t < nb * 64; t += blockDim.x) Hs[t] = (T)Hred[t];
@@ -159,25 +201,25 @@ __device__ __forceinline__ void k_tupdate_dev(const int cta, const int ncta, int
     cp_async_wait_1();
     __syncthreads();
     T* st = stages + (it & 1) * sstride;
-    T* Xs = st + nb * TR * 8;                               // W tile, overwritten by X
+    T* Xs = st + (size_t)nb * BlockStride<T>::value;                               // W tile, overwritten by X
     // phase 1: X = W - Q H, 4 columns per thread
     for (int p = tid; p < TR * 2; p += blockDim.x) {
       const int r = p >> 1, c0 = 4 * (p & 1);
       T x[4];
-#pragma unroll
-      for (int v = 0; v < 4; ++v) x[v] = Xs[r * 8 + c0 + v];
+      lds4<T>(Xs + r * 8 + c0, x);
       for (int b = 0; b < nb; ++b) {
-        const T* qr = st + ((size_t)b * TR + r) * 8;
+        T q[8];
+        lds8<T>(st + (size_t)b * BlockStride<T>::value + (size_t)r * 8, q);
         const T* hb = Hs + b * 64 + c0;
 #pragma unroll
         for (int ap = 0; ap < 8; ++ap) {
-          const T q = qr[ap];
+          T h[4];
+          lds4<T>(hb + ap * 8, h);
 #pragma unroll
-          for (int v = 0; v < 4; ++v) x[v] -= q * hb[ap * 8 + v];
+          for (int v = 0; v < 4; ++v) x[v] -= q[ap] * h[v];
         }
       }
-#pragma unroll
-      for (int v = 0; v < 4; ++v) Xs[r * 8 + c0 + v] = x[v];
+      sts4<T>(Xs + r * 8 + c0, x);
       const int row = tile * TR + r;
       if (row < n) {
 #pragma unroll
@@ -192,7 +234,7 @@ __device__ __forceinline__ void k_tupdate_dev(const int cta, const int ncta, int
       const bool act = nitems <= 32 ? (u == 0 && sub < nsub) : item < nitems;
       if (act) {
         const int b = item >> 2, a0 = 2 * (item & 3);
-        accum_pair<T>((b < nb ? st + (size_t)b * TR * 8 : Xs) + a0, Xs, grp + 8 * sub, 8 * nsub, acc[u]);
+        accum_pair<T>((b < nb ? st + (size_t)b * BlockStride<T>::value : Xs) + a0, Xs, grp + 8 * sub, 8 * nsub, acc[u]);
       }
     }
     __syncthreads();
@@ -237,7 +279,7 @@ __device__ __forceinline__ void k_tfinalize_dev(const int cta, const int ncta, i
   constexpr int TR = TileRows<T>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* stages = reinterpret_cast<T*>(smem_raw);
-  const int sstride = (nb + 1) * TR * 8;
+  const int sstride = (nb + 1) * BlockStride<T>::value;
   T* Hs = stages + 2 * sstride;
   T* Ri = Hs + 8 * 64;
   __shared__ int dfc[8];
@@ -256,25 +298,25 @@ __device__ __forceinline__ void k_tfinalize_dev(const int cta, const int ncta, i
     cp_async_wait_1();
     __syncthreads();
     T* st = stages + (it & 1) * sstride;
-    T* Xs = st + nb * TR * 8;
+    T* Xs = st + (size_t)nb * BlockStride<T>::value;
     for (int p = tid; p < TR * 2; p += blockDim.x) {
       const int r = p >> 1, c0 = 4 * (p & 1);
       T x[4];
-#pragma unroll
-      for (int v = 0; v < 4; ++v) x[v] = Xs[r * 8 + c0 + v];
+      lds4<T>(Xs + r * 8 + c0, x);
       for (int b = 0; b < nb; ++b) {
-        const T* qr = st + ((size_t)b * TR + r) * 8;
+        T q[8];
+        lds8<T>(st + (size_t)b * BlockStride<T>::value + (size_t)r * 8, q);
         const T* hb = Hs + b * 64 + c0;
 #pragma unroll
         for (int ap = 0; ap < 8; ++ap) {
-          const T q = qr[ap];
+          T h[4];
+          lds4<T>(hb + ap * 8, h);
 #pragma unroll
-          for (int v = 0; v < 4; ++v) x[v] -= q * hb[ap * 8 + v];
+          for (int v = 0; v < 4; ++v) x[v] -= q[ap] * h[v];
         }
       }
       __syncwarp();
-#pragma unroll
-      for (int v = 0; v < 4; ++v) Xs[r * 8 + c0 + v] = x[v];
+      sts4<T>(Xs + r * 8 + c0, x);
     }
     __syncthreads();
     for (int p = tid; p < TR * 2; p += blockDim.x) {
@@ -310,7 +352,7 @@ __device__ __forceinline__ void k_trestart_dev(const int cta, const int ncta, in
   constexpr int TR = TileRows<T>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* stages = reinterpret_cast<T*>(smem_raw);
-  const int sstride = nbk * TR * 8;
+  const int sstride = nbk * BlockStride<T>::value;
   T* Ys = stages + 2 * sstride;                       // J x ncol
   const int J = nbk * 8, ncol = nout * 8;
   const int tid = threadIdx.x;
@@ -337,7 +379,7 @@ __device__ __forceinline__ void k_trestart_dev(const int cta, const int ncta, in
 #pragma unroll
       for (int v = 0; v < 8; ++v) { acc0[v] = (T)0; acc1[v] = (T)0; }
       for (int b = 0; b < nbk; ++b) {
-        const T* qr0 = st + ((size_t)b * TR + r0) * 8;
+        const T* qr0 = st + (size_t)b * BlockStride<T>::value + (size_t)r0 * 8;
         const T* qr1 = qr0 + 8;
 #pragma unroll
         for (int a = 0; a < 8; ++a) {

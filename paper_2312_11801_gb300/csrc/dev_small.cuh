@@ -313,111 +313,6 @@ __device__ __forceinline__ void k_chol_block_dev(DevLanczos* lz, const double* U
   }
 }
 
-// ---- Jacobi sweeps of a 32 x 32 matrix on one warp, in registers (FP32) ----------------------
-// Lane l keeps row l of A and row l of the rotation product V.  The index pairs of a round
-// are the positions (2k, 2k + 1); after the round, rows and columns of A and the columns
-// of V move by a fixed permutation of positions (the round-robin rotation that keeps
-// slot 0 and turns slots 1..31, with slot i at position 2i and slot 31 - i at 2i + 1), so
-// every index pair shares a rotation once every 31 rounds.  Row moves are shuffles;
-// column moves are compile-time renamings of registers.  Work stays in position space:
-// the diagonal and the columns of V that come back are the eigenvalues and the matching
-// eigenvectors.
-__host__ __device__ constexpr int jw_slot_of_pos(int x) { return (x & 1) ? 31 - (x >> 1) : (x >> 1); }
-__host__ __device__ constexpr int jw_pos_of_slot(int i) { return i <= 15 ? 2 * i : 2 * (31 - i) + 1; }
-__host__ __device__ constexpr int jw_prev_slot(int i) { return i == 0 ? 0 : (i == 1 ? 31 : i - 1); }
-__host__ __device__ constexpr int jw_perm(int x) { return jw_pos_of_slot(jw_prev_slot(jw_slot_of_pos(x))); }
-
-// A and V in shared memory, row stride ld; V is overwritten (it starts as the identity).
-// Returns the number of sweeps taken.  Stops when the off-diagonal Frobenius norm is at
-// most eps times the whole norm, or after max_sweeps.
-__device__ __forceinline__ int jacobi_warp32(float* A, float* Vm, int ld, int max_sweeps, float eps,
-                                             float skip) {
-  const int lane = threadIdx.x & 31;
-  const bool even = (lane & 1) == 0;
-  const int src = jw_perm(lane);
-  float a[32], v[32];
-#pragma unroll
-  for (int c = 0; c < 32; ++c) {
-    a[c] = A[lane * ld + c];
-    v[c] = (c == lane) ? 1.f : 0.f;
-  }
-  float dg = A[lane * ld + lane];
-  int sweeps = 0;
-  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    double tot = 0.0, dd = 0.0;
-#pragma unroll
-    for (int c = 0; c < 32; ++c) {
-      tot += (double)a[c] * (double)a[c];
-      if (c == lane) dd = (double)a[c] * (double)a[c];
-    }
-    double off = tot - dd;
-    for (int o = 16; o > 0; o >>= 1) {
-      off += __shfl_xor_sync(FULL, off, o);
-      tot += __shfl_xor_sync(FULL, tot, o);
-    }
-    if (off <= (double)eps * (double)eps * tot) break;
-    ++sweeps;
-    for (int round = 0; round < 31; ++round) {
-      // rotation of the pair (2k, 2k + 1) = (lane & ~1, lane | 1), from the even lane's A[p][q]
-      float apq_own = 0.f;
-#pragma unroll
-      for (int c = 0; c < 32; ++c) apq_own = (c == (lane ^ 1)) ? a[c] : apq_own;
-      const float apq = __shfl_sync(FULL, apq_own, lane & ~1);
-      const float dpart = __shfl_xor_sync(FULL, dg, 1);
-      const float app = even ? dg : dpart, aqq = even ? dpart : dg;
-      float cs = 1.f, sn = 0.f;
-      if (apq != 0.f && fabsf(apq) > skip * sqrtf(fabsf(app * aqq))) {
-        const float tau = (aqq - app) / (2.f * apq);
-        float t;
-        if (fabsf(tau) > 1e18f) t = 0.5f / tau;
-        else t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(tau * tau + 1.f));
-        cs = 1.f / sqrtf(t * t + 1.f);
-        sn = t * cs;
-      }
-      // rows: [p; q] <- [c -s; s c] [p; q]
-#pragma unroll
-      for (int c = 0; c < 32; ++c) {
-        const float o = __shfl_xor_sync(FULL, a[c], 1);
-        a[c] = even ? (cs * a[c] - sn * o) : (sn * o + cs * a[c]);
-      }
-      // columns of A and V: [p q] <- [p q] [c s; -s c], every pair with its own rotation
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const float ck = __shfl_sync(FULL, cs, 2 * k), sk = __shfl_sync(FULL, sn, 2 * k);
-        float x = a[2 * k], y = a[2 * k + 1];
-        a[2 * k] = ck * x - sk * y;
-        a[2 * k + 1] = sk * x + ck * y;
-        x = v[2 * k];
-        y = v[2 * k + 1];
-        v[2 * k] = ck * x - sk * y;
-        v[2 * k + 1] = sk * x + ck * y;
-      }
-      dg = even ? (cs * cs * app - 2.f * cs * sn * apq + sn * sn * aqq)
-                : (sn * sn * app + 2.f * cs * sn * apq + cs * cs * aqq);
-      // move to the next round's positions: rows across lanes, columns within registers
-#pragma unroll
-      for (int c = 0; c < 32; ++c) a[c] = __shfl_sync(FULL, a[c], src);
-      dg = __shfl_sync(FULL, dg, src);
-      float t[32];
-#pragma unroll
-      for (int x = 0; x < 32; ++x) t[x] = a[jw_perm(x)];
-#pragma unroll
-      for (int x = 0; x < 32; ++x) a[x] = t[x];
-#pragma unroll
-      for (int x = 0; x < 32; ++x) t[x] = v[jw_perm(x)];
-#pragma unroll
-      for (int x = 0; x < 32; ++x) v[x] = t[x];
-    }
-  }
-#pragma unroll
-  for (int c = 0; c < 32; ++c) {
-    A[lane * ld + c] = a[c];
-    Vm[lane * ld + c] = v[c];
-  }
-  __syncwarp();
-  return sweeps;
-}
-
 // ---- Rayleigh-Ritz: eigen-decomposition of T by parallel cyclic Jacobi ------------------------
 // S is the arithmetic of the whole Ritz step (FP32 in mixed mode, where GB300's FP64 rate
 // would make this one CTA the bottleneck; FP64 in the plain mode).  The J/2 rotations
@@ -471,93 +366,82 @@ __device__ __forceinline__ void k_ritz_dev(DevLanczos* lz, int kc, double tol, i
     return;
   }
   const S skip = (S)(jac_eps * 1e-2), big = (S)1e18;
-  if constexpr (J == 32 && sizeof(S) == 4) {
-    // one warp, registers only (the other warps wait at the barrier)
-    (void)big;
-    if (warp == 0) {
-      const int sw = jacobi_warp32(reinterpret_cast<float*>(A), reinterpret_cast<float*>(Vv), LD,
-                                   max_sweeps, (float)jac_eps, (float)skip);
-      if (lane == 0) lz->sweeps += sw;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int t = tid; t < J * J; t += blockDim.x) {
+      const int i = t / J, j = t % J;
+      const double x = (double)A[i * LD + j];
+      tot += x * x;
+      if (i != j) off += x * x;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    }
+    if (lane == 0) { wred[0][warp] = off; wred[1][warp] = tot; }
+    __syncthreads();
+    if (tid == 0) {
+      double o2 = 0.0, t2 = 0.0;
+      for (int w = 0; w < nw; ++w) { o2 += wred[0][w]; t2 += wred[1][w]; }
+      stop = (o2 <= jac_eps * jac_eps * t2) ? 1 : 0;
     }
     __syncthreads();
-  } else {
-    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-      double off = 0.0, tot = 0.0;
-      for (int t = tid; t < J * J; t += blockDim.x) {
-        const int i = t / J, j = t % J;
-        const double x = (double)A[i * LD + j];
-        tot += x * x;
-        if (i != j) off += x * x;
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        off += __shfl_xor_sync(0xffffffffu, off, o);
-        tot += __shfl_xor_sync(0xffffffffu, tot, o);
-      }
-      if (lane == 0) { wred[0][warp] = off; wred[1][warp] = tot; }
-      __syncthreads();
-      if (tid == 0) {
-        double o2 = 0.0, t2 = 0.0;
-        for (int w = 0; w < nw; ++w) { o2 += wred[0][w]; t2 += wred[1][w]; }
-        stop = (o2 <= jac_eps * jac_eps * t2) ? 1 : 0;
-      }
-      __syncthreads();
-      if (stop) break;
-      if (tid == 0) lz->sweeps += 1;
-      for (int round = 0; round < J - 1; ++round) {
-        if (tid < half) {
-          // circle method: position 0 fixed, the others rotate
-          const int k = tid;
-          const int posA = k, posB = J - 1 - k;
-          const int pa = posA == 0 ? 0 : 1 + ((posA - 1 + round) % (J - 1));
-          const int pb = 1 + ((posB - 1 + round) % (J - 1));
-          const int p = min(pa, pb), q = max(pa, pb);
-          pp[k] = p;
-          qq[k] = q;
-          const S apq = A[p * LD + q];
-          S c = (S)1, sv = (S)0;
-          const S app = A[p * LD + p], aqq = A[q * LD + q];
-          // all in S: an FP64 sqrt here would be a long FP64 sequence every round
-          if (apq != (S)0 && fabs(apq) > skip * sqrt(fabs(app * aqq))) {
-            const S tau = (aqq - app) / ((S)2 * apq);
-            S t;
-            if (fabs(tau) > big) t = (S)0.5 / tau;
-            else t = (tau >= (S)0 ? (S)1 : (S)-1) / (fabs(tau) + sqrt(tau * tau + (S)1));
-            c = (S)1 / sqrt(t * t + (S)1);
-            sv = t * c;
-          }
-          cs[k] = c;
-          sn[k] = sv;
+    if (stop) break;
+    if (tid == 0) lz->sweeps += 1;
+    for (int round = 0; round < J - 1; ++round) {
+      if (tid < half) {
+        // circle method: position 0 fixed, the others rotate
+        const int k = tid;
+        const int posA = k, posB = J - 1 - k;
+        const int pa = posA == 0 ? 0 : 1 + ((posA - 1 + round) % (J - 1));
+        const int pb = 1 + ((posB - 1 + round) % (J - 1));
+        const int p = min(pa, pb), q = max(pa, pb);
+        pp[k] = p;
+        qq[k] = q;
+        const S apq = A[p * LD + q];
+        S c = (S)1, sv = (S)0;
+        const S app = A[p * LD + p], aqq = A[q * LD + q];
+        // all in S: an FP64 sqrt here would be a long FP64 sequence every round
+        if (apq != (S)0 && fabs(apq) > skip * sqrt(fabs(app * aqq))) {
+          const S tau = (aqq - app) / ((S)2 * apq);
+          S t;
+          if (fabs(tau) > big) t = (S)0.5 / tau;
+          else t = (tau >= (S)0 ? (S)1 : (S)-1) / (fabs(tau) + sqrt(tau * tau + (S)1));
+          c = (S)1 / sqrt(t * t + (S)1);
+          sv = t * c;
         }
-        __syncthreads();
-        // A <- G^T A G on 2 x 2 blocks; V <- V G (index arithmetic on powers of two)
-        constexpr int NBLK = half * half, NITEM = half * half + J * half;
-        for (int t = tid; t < NITEM; t += blockDim.x) {
-          if (t < NBLK) {
-            const int k1 = t / half, k2 = t % half;
-            const int p1 = pp[k1], q1 = qq[k1], p2 = pp[k2], q2 = qq[k2];
-            const S c1 = cs[k1], s1 = sn[k1], c2 = cs[k2], s2 = sn[k2];
-            const S a = A[p1 * LD + p2], b = A[p1 * LD + q2];
-            const S cc = A[q1 * LD + p2], d = A[q1 * LD + q2];
-            // rows: [p1; q1] <- [c1 -s1; s1 c1] [p1; q1]
-            const S ra = c1 * a - s1 * cc, rb = c1 * b - s1 * d;
-            const S rc = s1 * a + c1 * cc, rd = s1 * b + c1 * d;
-            // cols: [p2 q2] <- [p2 q2] [c2 s2; -s2 c2]
-            A[p1 * LD + p2] = c2 * ra - s2 * rb;
-            A[p1 * LD + q2] = s2 * ra + c2 * rb;
-            A[q1 * LD + p2] = c2 * rc - s2 * rd;
-            A[q1 * LD + q2] = s2 * rc + c2 * rd;
-          } else {
-            const int u = t - NBLK;
-            const int k = u / J, row = u % J;
-            const S c = cs[k], sv = sn[k];
-            const int p = pp[k], q = qq[k];
-            const S vp = Vv[row * LD + p], vq = Vv[row * LD + q];
-            Vv[row * LD + p] = c * vp - sv * vq;
-            Vv[row * LD + q] = sv * vp + c * vq;
-          }
-        }
-        __syncthreads();
+        cs[k] = c;
+        sn[k] = sv;
       }
+      __syncthreads();
+      // A <- G^T A G on 2 x 2 blocks; V <- V G (index arithmetic on powers of two)
+      constexpr int NBLK = half * half, NITEM = half * half + J * half;
+      for (int t = tid; t < NITEM; t += blockDim.x) {
+        if (t < NBLK) {
+          const int k1 = t / half, k2 = t % half;
+          const int p1 = pp[k1], q1 = qq[k1], p2 = pp[k2], q2 = qq[k2];
+          const S c1 = cs[k1], s1 = sn[k1], c2 = cs[k2], s2 = sn[k2];
+          const S a = A[p1 * LD + p2], b = A[p1 * LD + q2];
+          const S cc = A[q1 * LD + p2], d = A[q1 * LD + q2];
+          // rows: [p1; q1] <- [c1 -s1; s1 c1] [p1; q1]
+          const S ra = c1 * a - s1 * cc, rb = c1 * b - s1 * d;
+          const S rc = s1 * a + c1 * cc, rd = s1 * b + c1 * d;
+          // cols: [p2 q2] <- [p2 q2] [c2 s2; -s2 c2]
+          A[p1 * LD + p2] = c2 * ra - s2 * rb;
+          A[p1 * LD + q2] = s2 * ra + c2 * rb;
+          A[q1 * LD + p2] = c2 * rc - s2 * rd;
+          A[q1 * LD + q2] = s2 * rc + c2 * rd;
+        } else {
+          const int u = t - NBLK;
+          const int k = u / J, row = u % J;
+          const S c = cs[k], sv = sn[k];
+          const int p = pp[k], q = qq[k];
+          const S vp = Vv[row * LD + p], vq = Vv[row * LD + q];
+          Vv[row * LD + p] = c * vp - sv * vq;
+          Vv[row * LD + q] = sv * vp + c * vq;
+        }
+      }
+      __syncthreads();
     }
   }
   // descending order under a strict total order (value, then index)
@@ -691,52 +575,49 @@ __device__ __forceinline__ double aug_at(const double* aug, int r, int c) {
   return aug[idx * 16 + (r % 4) * 4 + (c % 4)];
 }
 
-// One warp runs the whole IPM: every step of a Newton iteration is a lane-strided loop
-// over k-sized data in shared memory, ordered by __syncwarp only.  The FP64 work of an
-// iteration is about 26K multiply-adds (dominated by the 36 x 36 elimination), so on
-// GB300's FP64 rate the iteration is bound by that arithmetic, not by CTA barriers.
-// Callers run it on lanes 0..31 of one warp (the per-step kernel launches 32 threads).
 __device__ __forceinline__ void k_ipm_dev(DevScalars* sc, const double* USBS_RESTRICT red, int kc,
-                                          double alpha, double rho, double mu_tol, int max_iter,
-                                          int first_pass) {
+                                             double alpha, double rho, double mu_tol, int max_iter,
+                                             int first_pass) {
   __shared__ IpmShared sh;
-  __shared__ int pq[KSV][2];   // svec position u -> (p, q), p >= q, column-major lower triangle
-  const int lane = threadIdx.x & 31;
+  const int tid = threadIdx.x;
   const int K = kc * (kc + 1) / 2;
   const double* aug = red + RED_AUG;
   const double* vec = red + RED_VEC;
   const double* vc = red + RED_VC;
-  if (lane == 0) {
+  if (tid == 0) {
     int u = 0;
     for (int q = 0; q < kc; ++q)
-      for (int p = q; p < kc; ++p) {
-        sh.map[u] = svec_idx8(p, q);
-        pq[u][0] = p;
-        pq[u][1] = q;
-        ++u;
-      }
+      for (int p = q; p < kc; ++p) sh.map[u++] = svec_idx8(p, q);
     sh.has_eta = sc->tr > 0.0 ? 1 : 0;
     sc->has_eta = sh.has_eta;
   }
-  __syncwarp();
+  __syncthreads();
   const int has_eta = sh.has_eta;
   const double tr = sc->tr, cx = sc->cx;
   const double a2r = alpha * alpha / rho;
-  for (int t = lane; t < K * K; t += 32) {
+  for (int t = tid; t < K * K; t += blockDim.x) {
     const int i = t / K, j = t % K;
     sh.Q[t] = a2r * aug_at(aug, sh.map[i], sh.map[j]);
   }
-  for (int u = lane; u < K; u += 32) {
-    const int gi = sh.map[u];
-    sh.q12[u] = has_eta ? a2r / tr * aug_at(aug, gi, 36) : 0.0;
+  if (tid < K) {
+    const int gi = sh.map[tid];
+    sh.q12[tid] = has_eta ? a2r / tr * aug_at(aug, gi, 36) : 0.0;
     const double gtw = first_pass ? aug_at(aug, gi, 37) : vec[gi];
-    const int p = pq[u][0], q = pq[u][1];
+    // svec of V^T C V (k_c x k_c block)
+    int p = 0, q = 0;
+    {
+      int u = tid;
+      for (q = 0; q < kc; ++q) {
+        if (u < kc - q) { p = q + u; break; }
+        u -= kc - q;
+      }
+    }
     const double vcpq = 0.5 * (vc[p * 8 + q] + vc[q * 8 + p]);
     const double svc = (p == q) ? vcpq : SQ2 * vcpq;
-    sh.h1[u] = alpha * (gtw - svc);
-    sh.v[u] = (p == q) ? 1.0 : 0.0;
+    sh.h1[tid] = alpha * (gtw - svc);
+    sh.v[tid] = (p == q) ? 1.0 : 0.0;
   }
-  if (lane == 0) {
+  if (tid == 0) {
     sh.q22 = has_eta ? a2r / (tr * tr) * aug_at(aug, 36, 36) : 0.0;
     const double axw = first_pass ? aug_at(aug, 36, 37) : vec[36];
     sh.h2 = has_eta ? alpha * (axw - cx) / tr : 0.0;
@@ -753,37 +634,51 @@ __device__ __forceinline__ void k_ipm_dev(DevScalars* sc, const double* USBS_RES
     sh.done = 0;
     sh.iters = 0;
   }
-  __syncwarp();
-  const int LDL = K + 1;
+  __syncthreads();
+  const int lane = tid & 31, warp = tid >> 5;
   for (int it = 1; it <= max_iter; ++it) {
     // S^-1 (warp-cooperative Cholesky and inverse)
-    warp_chol(sh.S, sh.Lc, kc);
-    warp_spd_inverse(sh.Lc, sh.work, sh.Sinv, kc);
-    for (int u = lane; u < K; u += 32) {
-      const int p = pq[u][0], q = pq[u][1];
+    if (warp == 0) {
+      warp_chol(sh.S, sh.Lc, kc);
+      warp_spd_inverse(sh.Lc, sh.work, sh.Sinv, kc);
+    }
+    __syncthreads();
+    if (tid < K) {
+      int p = 0, q = 0;
+      int u = tid;
+      for (q = 0; q < kc; ++q) {
+        if (u < kc - q) { p = q + u; break; }
+        u -= kc - q;
+      }
       const double f = (p == q) ? 1.0 : SQ2;
-      sh.s[u] = f * sh.S[p * 8 + q];
-      sh.t[u] = f * sh.T[p * 8 + q];
-      sh.sinv[u] = f * sh.Sinv[p * 8 + q];
+      sh.s[tid] = f * sh.S[p * 8 + q];
+      sh.t[tid] = f * sh.T[p * 8 + q];
+      sh.sinv[tid] = f * sh.Sinv[p * 8 + q];
     }
     // T (x)_s S^-1 entry by entry: (1/(s_a s_b)) (H_jk G_il + G_jk H_il + H_jl G_ik + G_jl H_ik)
     // with G = T, H = S^-1, a = (i, j), b = (k, l), s = 2 on the diagonal and sqrt(2) off it
-    for (int t = lane; t < K * K; t += 32) {
+    for (int t = tid; t < K * K; t += blockDim.x) {
       const int ra = t / K, cb = t % K;
-      const int i = pq[ra][0], j = pq[ra][1], k = pq[cb][0], l = pq[cb][1];
+      int i = 0, j = 0, k = 0, l = 0;
+      {
+        int u = ra;
+        for (j = 0; j < kc; ++j) { if (u < kc - j) { i = j + u; break; } u -= kc - j; }
+        u = cb;
+        for (l = 0; l < kc; ++l) { if (u < kc - l) { k = l + u; break; } u -= kc - l; }
+      }
       const double inv_s = ((i == j) ? 0.5 : 1.0 / SQ2) * ((k == l) ? 0.5 : 1.0 / SQ2);
       const double* G = sh.T;
       const double* H = sh.Sinv;
       sh.TS[t] = (H[j * 8 + k] * G[i * 8 + l] + G[j * 8 + k] * H[i * 8 + l] +
                   H[j * 8 + l] * G[i * 8 + k] + G[j * 8 + l] * H[i * 8 + k]) * inv_s;
     }
-    __syncwarp();
-    for (int u = lane; u < K; u += 32) {
-      double f1 = sh.h1[u] - sh.t[u] + sh.omega * sh.v[u] + sh.eta * sh.q12[u];
-      for (int c = 0; c < K; ++c) f1 += sh.Q[u * K + c] * sh.s[c];
-      sh.F1[u] = f1;
+    __syncthreads();
+    if (tid < K) {
+      double f1 = sh.h1[tid] - sh.t[tid] + sh.omega * sh.v[tid] + sh.eta * sh.q12[tid];
+      for (int c = 0; c < K; ++c) f1 += sh.Q[tid * K + c] * sh.s[c];
+      sh.F1[tid] = f1;
     }
-    if (lane == 0) {
+    if (tid == 32) {
       double trS = 0.0;
       for (int p = 0; p < kc; ++p) trS += sh.S[p * 8 + p];
       const double slack = 1.0 - trS - sh.eta;
@@ -798,12 +693,12 @@ __device__ __forceinline__ void k_ipm_dev(DevScalars* sc, const double* USBS_RES
         sh.det = sh.kappa1 * sh.kappa2 + 1.0;
       }
     }
-    __syncwarp();
+    __syncthreads();
     // assemble [L | rhs] (eq. delta_S_linear_system2)
     {
       const double idet = has_eta ? 1.0 / sh.det : 0.0, ik1 = has_eta ? 0.0 : 1.0 / sh.kappa1;
-      for (int t = lane; t < K * LDL; t += 32) {
-        const int i = t / LDL, j = t % LDL;
+      for (int t = tid; t < K * (K + 1); t += blockDim.x) {
+        const int i = t / (K + 1), j = t % (K + 1);
         double val;
         if (j < K) {
           val = sh.Q[i * K + j] + sh.TS[i * K + j];
@@ -822,55 +717,63 @@ __device__ __forceinline__ void k_ipm_dev(DevScalars* sc, const double* USBS_RES
         sh.L[t] = val;
       }
     }
-    if (lane == 0) sh.piv = 0;
-    __syncwarp();
+    __syncthreads();
     // Gaussian elimination with partial pivoting
+    const int LDL = K + 1;
+    if (tid == 0) sh.piv = 0;
+    __syncthreads();
     for (int p = 0; p < K; ++p) {
-      double best = -1.0;
-      int bi = p;
-      for (int r = p + lane; r < K; r += 32) {
-        const double x = fabs(sh.L[r * LDL + p]);
-        if (x > best) { best = x; bi = r; }
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        const double ob = __shfl_xor_sync(FULL, best, o);
-        const int oi = __shfl_xor_sync(FULL, bi, o);
-        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-      }
-      if (bi != p)
-        for (int c = p + lane; c < LDL; c += 32) {
-          const double x = sh.L[p * LDL + c];
-          sh.L[p * LDL + c] = sh.L[bi * LDL + c];
-          sh.L[bi * LDL + c] = x;
+      if (warp == 0) {
+        double best = -1.0;
+        int bi = p;
+        for (int r = p + lane; r < K; r += 32) {
+          const double x = fabs(sh.L[r * LDL + p]);
+          if (x > best) { best = x; bi = r; }
         }
-      __syncwarp();
-      // an exactly singular system (possible at degenerate optima): mark the direction
-      // unusable instead of dividing by zero
-      const double pv = sh.L[p * LDL + p];
-      const double ipv = (fabs(pv) > 1e-300) ? 1.0 / pv : 0.0;
-      if (lane == 0) {
-        sh.fcol[p] = ipv;
-        if (!(fabs(pv) > 1e-300)) sh.piv = -1;
+        for (int o = 16; o > 0; o >>= 1) {
+          const double ob = __shfl_xor_sync(FULL, best, o);
+          const int oi = __shfl_xor_sync(FULL, bi, o);
+          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (bi != p)
+          for (int c = p + lane; c < LDL; c += 32) {
+            const double x = sh.L[p * LDL + c];
+            sh.L[p * LDL + c] = sh.L[bi * LDL + c];
+            sh.L[bi * LDL + c] = x;
+          }
+        __syncwarp();
+        if (lane == 0) {
+          // an exactly singular system (possible at degenerate optima): mark the
+          // direction unusable instead of dividing by zero
+          const double pv = sh.L[p * LDL + p];
+          sh.fcol[p] = (fabs(pv) > 1e-300) ? 1.0 / pv : 0.0;
+          if (!(fabs(pv) > 1e-300)) sh.piv = -1;
+        }
       }
+      __syncthreads();
+      const double ipv = sh.fcol[p];
       const int rows = K - p - 1, cols = LDL - p - 1;
-      for (int t = lane; t < rows * cols; t += 32) {
+      for (int t = tid; t < rows * cols; t += blockDim.x) {
         const int r = p + 1 + t / cols, c = p + 1 + t % cols;
         sh.L[r * LDL + c] -= sh.L[r * LDL + p] * ipv * sh.L[p * LDL + c];
       }
-      __syncwarp();
+      __syncthreads();
     }
-    // back substitution with the reciprocal pivots kept in fcol
-    for (int r = K - 1; r >= 0; --r) {
-      double x = 0.0;
-      if (lane == 0) {
-        x = sh.L[r * LDL + K] * sh.fcol[r];
-        sh.ds[r] = x;
+    // back substitution (warp 0) with the reciprocal pivots kept in fcol
+    if (warp == 0) {
+      for (int r = K - 1; r >= 0; --r) {
+        double x = 0.0;
+        if (lane == 0) {
+          x = sh.L[r * LDL + K] * sh.fcol[r];
+          sh.ds[r] = x;
+        }
+        x = __shfl_sync(FULL, x, 0);
+        for (int i = lane; i < r; i += 32) sh.L[i * LDL + K] -= sh.L[i * LDL + r] * x;
+        __syncwarp();
       }
-      x = __shfl_sync(FULL, x, 0);
-      for (int i = lane; i < r; i += 32) sh.L[i * LDL + K] -= sh.L[i * LDL + r] * x;
-      __syncwarp();
     }
-    if (lane == 0) {
+    __syncthreads();
+    if (tid == 0) {
       double vds = 0.0;
       for (int c = 0; c < K; ++c) vds += sh.v[c] * sh.ds[c];
       if (has_eta) {
@@ -886,24 +789,25 @@ __device__ __forceinline__ void k_ipm_dev(DevScalars* sc, const double* USBS_RES
         sh.dzeta = 0.0;
       }
     }
-    for (int r = lane; r < K; r += 32) {
+    if (tid >= 32 && tid < 32 + K) {
+      const int r = tid - 32;
       double x = sh.mu * sh.sinv[r] - sh.t[r];
       for (int c = 0; c < K; ++c) x -= sh.TS[r * K + c] * sh.ds[c];
       sh.dt[r] = x;
     }
-    __syncwarp();
+    __syncthreads();
     // a non-finite Newton direction (singular system): keep the current strictly
     // feasible iterate and stop
-    if (lane == 0) {
+    if (tid == 0) {
       bool fin = isfinite(sh.deta) && isfinite(sh.domega) && isfinite(sh.dzeta) && sh.piv >= 0;
       for (int c = 0; c < K && fin; ++c) fin = isfinite(sh.ds[c]) && isfinite(sh.dt[c]);
       sh.done = fin ? 0 : 2;
     }
-    __syncwarp();
+    __syncthreads();
     if (sh.done == 2) break;
-    for (int t = lane; t < 64; t += 32) {
+    if (tid < 64) {
       // smat of ds, dt
-      const int p = t / 8, q = t % 8;
+      const int p = tid / 8, q = tid % 8;
       double vs = 0.0, vt = 0.0;
       if (p < kc && q < kc) {
         const int pi = max(p, q), qi = min(p, q);
@@ -912,48 +816,58 @@ __device__ __forceinline__ void k_ipm_dev(DevScalars* sc, const double* USBS_RES
         vs = f * sh.ds[u];
         vt = f * sh.dt[u];
       }
-      sh.dS[t] = vs;
-      sh.dT[t] = vt;
+      sh.dS[tid] = vs;
+      sh.dT[tid] = vt;
     }
-    if (lane == 0) sh.delta = 1.0;
-    __syncwarp();
-    // backtracking: halve until S and T are positive definite and the scalars and trace
-    // slack positive, then take 0.95 delta
+    if (tid == 0) sh.delta = 1.0;
+    __syncthreads();
+    // backtracking: halve until strictly feasible (warps 0 and 1 test S and T), then 0.95 delta
     for (int ls = 0; ls < 80; ++ls) {
       const double delta = sh.delta;
-      for (int t = lane; t < 64; t += 32) {
-        sh.St[t] = sh.S[t] + delta * sh.dS[t];
-        sh.Tt[t] = sh.T[t] + delta * sh.dT[t];
+      if (tid < 64) {
+        const int p = tid / 8, q = tid % 8;
+        sh.St[tid] = sh.S[tid] + delta * sh.dS[tid];
+        sh.Tt[tid] = sh.T[tid] + delta * sh.dT[tid];
+        (void)p; (void)q;
       }
-      __syncwarp();
-      const bool okS = warp_chol(sh.St, nullptr, kc);
-      const bool okT = warp_chol(sh.Tt, nullptr, kc);
-      if (lane == 0) {
+      __syncthreads();
+      bool okw = true;
+      if (warp == 0) okw = warp_chol(sh.St, nullptr, kc);
+      if (warp == 1) okw = warp_chol(sh.Tt, nullptr, kc);
+      if (lane == 0 && warp < 2) sh.fcol[warp] = okw ? 1.0 : 0.0;
+      __syncthreads();
+      if (tid == 0) {
         double trS = 0.0;
         for (int p = 0; p < kc; ++p) trS += sh.St[p * 8 + p];
         const double en = sh.eta + delta * sh.deta, zn = sh.zeta + delta * sh.dzeta;
         const double on = sh.omega + delta * sh.domega;
-        bool ok = on > 0.0 && (1.0 - trS - en) > 0.0 && okS && okT;
+        bool ok = on > 0.0 && (1.0 - trS - en) > 0.0 && sh.fcol[0] > 0.5 && sh.fcol[1] > 0.5;
         if (has_eta) ok = ok && en > 0.0 && zn > 0.0;
         sh.done = ok ? 1 : 0;
         if (!ok) sh.delta = 0.5 * delta;
       }
-      __syncwarp();
+      __syncthreads();
       if (sh.done) break;
     }
+    __syncthreads();
     const double delta = 0.95 * sh.delta;
-    for (int t = lane; t < 64; t += 32) {
-      const int p = t / 8, q = t % 8;
-      double sv = sh.S[t], tv = sh.T[t];
+    if (tid < 64) {
+      const int p = tid / 8, q = tid % 8;
+      double sv = sh.S[tid], tv = sh.T[tid];
       if (p < kc && q < kc) {
-        sv = sh.S[t] + 0.5 * delta * (sh.dS[p * 8 + q] + sh.dS[q * 8 + p]);
-        tv = sh.T[t] + 0.5 * delta * (sh.dT[p * 8 + q] + sh.dT[q * 8 + p]);
+        sv = sh.S[tid] + 0.5 * delta * (sh.dS[p * 8 + q] + sh.dS[q * 8 + p]);
+        tv = sh.T[tid] + 0.5 * delta * (sh.dT[p * 8 + q] + sh.dT[q * 8 + p]);
       }
-      sh.S[t] = sv;
-      sh.T[t] = tv;
+      sh.St[tid] = sv;
+      sh.Tt[tid] = tv;
     }
-    __syncwarp();
-    if (lane == 0) {
+    __syncthreads();
+    if (tid < 64) {
+      sh.S[tid] = sh.St[tid];
+      sh.T[tid] = sh.Tt[tid];
+    }
+    __syncthreads();
+    if (tid == 0) {
       sh.omega += delta * sh.domega;
       if (has_eta) {
         sh.eta += delta * sh.deta;
@@ -971,10 +885,10 @@ __device__ __forceinline__ void k_ipm_dev(DevScalars* sc, const double* USBS_RES
       sh.iters = it;
       sh.done = (sh.mu < mu_tol || !isfinite(sh.mu)) ? 1 : 0;
     }
-    __syncwarp();
+    __syncthreads();
     if (sh.done) break;
   }
-  if (lane == 0) {
+  if (tid == 0) {
     for (int u = 0; u < 64; ++u) {
       sc->S_hat[u] = sh.S[u];
       sc->S[u] = alpha * sh.S[u];
@@ -987,7 +901,6 @@ __device__ __forceinline__ void k_ipm_dev(DevScalars* sc, const double* USBS_RES
     sc->ipm_iters += sh.iters;
     if (!isfinite(sh.mu) || !isfinite(sh.eta)) sc->status = USBS_ENUMERIC;
   }
-  __syncwarp();
 }
 
 // ---- model value, descent test, implicit primal update and gates ------------------------------

@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(256) k_trestart(int n, const T* __restrict__ Q
 
 template <typename T>
 size_t tile_smem(int nb, int extra) {
-  return sizeof(T) * (2 * (size_t)(nb + 1) * TileRows<T>::value * 8 + extra);
+  return sizeof(T) * (2 * (size_t)(nb + 1) * BlockStride<T>::value + extra);
 }
 
 template <typename T>
@@ -65,7 +65,7 @@ void set_attrs() {
     cudaFuncSetAttribute(k_tupdate<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_tfinalize<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_trestart<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(sizeof(T) * (2 * (size_t)8 * TileRows<T>::value * 8 + JMAX * 32)));
+                         (int)(sizeof(T) * (2 * (size_t)8 * BlockStride<T>::value + JMAX * 32)));
   });
 }
 
@@ -154,7 +154,7 @@ void Orth<T>::restart(Ctx* c, const void* Qb, int J, int nout, const double* Y, 
                       const void* resid, int resid_slot) {
   USBS_LAUNCH_B(c, USBS_KIND_RESTART, 8.0 * sizeof(T) * c->n * (J / 8 + nout + (resid ? 2 : 0)));
   set_attrs<T>();
-  const size_t sm = sizeof(T) * (2 * (size_t)(J / 8) * TileRows<T>::value * 8 + (size_t)J * nout * 8);
+  const size_t sm = sizeof(T) * (2 * (size_t)(J / 8) * BlockStride<T>::value + (size_t)J * nout * 8);
   k_trestart<T><<<orth_grid(c, c->n, (const void*)k_trestart<T>, sm), 256, sm, c->stream>>>(
       (int)c->n, (const T*)Qb, (size_t)c->n * 8, J / 8, nout, Y, (T*)out, (size_t)c->n * 8,
       (const T*)resid, resid_slot);

@@ -24,7 +24,7 @@ __global__ void __launch_bounds__(512) k_ritz(DevLanczos* lz, int kc, double tol
   k_ritz_dev<S, J>(lz, kc, tol, max_sweeps, jac_eps);
 }
 
-__global__ void __launch_bounds__(32) k_ipm(DevScalars* sc, const double* __restrict__ red, int kc,
+__global__ void __launch_bounds__(256) k_ipm(DevScalars* sc, const double* __restrict__ red, int kc,
                                              double alpha, double rho, double mu_tol, int max_iter,
                                              int first_pass) {
   k_ipm_dev(sc, red, kc, alpha, rho, mu_tol, max_iter, first_pass);
@@ -107,7 +107,7 @@ void launch_ritz(Ctx* c, int J, int keep) {
 
 void launch_ipm(Ctx* c, int first_pass) {
   USBS_LAUNCH(c, USBS_KIND_SMALL);
-  k_ipm<<<1, 32, 0, c->stream>>>(c->sc, c->red, c->kc, c->alpha, c->prm.rho, c->prm.ipm_mu_tol,
+  k_ipm<<<1, 256, 0, c->stream>>>(c->sc, c->red, c->kc, c->alpha, c->prm.rho, c->prm.ipm_mu_tol,
                                   c->prm.ipm_max_iter, first_pass);
 }
 
