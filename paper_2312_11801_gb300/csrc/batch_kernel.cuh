@@ -275,6 +275,7 @@ size_t batch_smem(int J) {
   size_t m = 0;
   m = std::max(m, sizeof(T) * (2 * (size_t)(nbmax + 1) * BlockStride<T>::value + 8 * 64 + 64));  // tiles
   m = std::max(m, sizeof(double) * 8 * 576);                                      // epilogues
+  m = std::max(m, tc_red_bytes(5));                                               // FP32 update
   m = std::max(m, sizeof(T) * (2 * (size_t)nbmax * BlockStride<T>::value + (size_t)J * (J / 2)));  // restart
   m = std::max(m, sizeof(T) * (4 * (size_t)J * (J + 1) + (size_t)J * J / 2));       // Ritz
   m = std::max(m, sizeof(T) * 128 * AUG + sizeof(double) * 4 * 880);              // gstats

@@ -82,6 +82,323 @@ __device__ __forceinline__ void load_tile(T* stage, const T* USBS_RESTRICT Q, si
   }
 }
 
+// ---- out = (W - Q H2) R^-1; deficient columns replaced by random vectors -----------------------
+__device__ __forceinline__ double hash_uniform_o(uint64_t seed, uint64_t row, uint64_t col) {
+  uint64_t z = seed + 0x9E3779B97F4A7C15ull * (row * 16 + col + 1);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z = z ^ (z >> 31);
+  return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
+
+
+// =============================================================================================
+// FP32 bodies on the tensor cores.  Every contraction of the tiles is an m16n8k8 TF32 MMA
+// (mma.sync) with FP32 accumulation.  TF32 keeps 10 mantissa bits, so each FP32 operand
+// is split into a TF32 high part and a TF32 low part (the rounding error of the high
+// part) and a product is taken as hi*hi + hi*lo + lo*hi: about 2^-21 relative, the
+// accuracy of the FP32 CUDA-core products these replace.
+// Fragment layout of m16n8k8 (g = lane / 4, t = lane % 4): A (16 x 8, row-major)
+// a0 (g, t), a1 (g+8, t), a2 (g, t+4), a3 (g+8, t+4); B (8 x 8) b0 (t, g), b1 (t+4, g);
+// C/D (16 x 8) c0 (g, 2t), c1 (g, 2t+1), c2 (g+8, 2t), c3 (g+8, 2t+1).
+// =============================================================================================
+__device__ __forceinline__ uint32_t tf32_of(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo) {
+  hi = tf32_of(x);
+  lo = tf32_of(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                         uint32_t a3, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+// D += A B with A given by four FP32 values and B by two, in split TF32 (small terms first)
+struct SplitB { uint32_t h0, h1, l0, l1; };
+__device__ __forceinline__ SplitB split_b(float b0, float b1) {
+  SplitB s;
+  tf32_split(b0, s.h0, s.l0);
+  tf32_split(b1, s.h1, s.l1);
+  return s;
+}
+__device__ __forceinline__ void mma3(float (&d)[4], float a0, float a1, float a2, float a3, const SplitB& b) {
+  uint32_t h0, h1, h2, h3, l0, l1, l2, l3;
+  tf32_split(a0, h0, l0);
+  tf32_split(a1, h1, l1);
+  tf32_split(a2, h2, l2);
+  tf32_split(a3, h3, l3);
+  mma_tf32(d, l0, l1, l2, l3, b.h0, b.h1);
+  mma_tf32(d, h0, h1, h2, h3, b.l0, b.l1);
+  mma_tf32(d, h0, h1, h2, h3, b.h0, b.h1);
+}
+
+// shared memory of the warp reduction of tc_reduce_xty with MAXP pairs: 8 x MAXP x 32 x 4
+// doubles (tproj: 4 pairs, 32 KB; tupdate: 5 pairs, 40 KB)
+constexpr size_t tc_red_bytes(int maxp) { return sizeof(double) * 8 * (size_t)maxp * 32 * 4; }
+
+// index of output (m, c) of a 16 x 8 D fragment: lane and register
+__device__ __forceinline__ int dfrag_lane(int m, int c) { return (m & 7) * 4 + (c >> 1); }
+__device__ __forceinline__ int dfrag_reg(int m, int c) { return ((m >> 3) << 1) | (c & 1); }
+
+// Sums of X_i^T Y over the tile's rows for the blocks of `blocks` (block i at stage
+// offset i * BS; block nblk-1 may be Y itself), accumulated per block pair in acc: pair p
+// covers blocks 2p and 2p+1 (rows m 0..7 and 8..15 of the MMA).  Warp w takes the 8-row
+// k-steps w and w + 8 of the 128-row tile.
+template <int MAXP>
+__device__ __forceinline__ void tc_accum_xty(const float* st, int nblk, const float* Y, int warp, int g, int t,
+                                             float (&acc)[MAXP][4]) {
+  constexpr int BS = BlockStride<float>::value;
+  for (int ks = warp; ks < 16; ks += 8) {
+    const int r0 = ks * 8;
+    const SplitB b = split_b(Y[(r0 + t) * 8 + g], Y[(r0 + t + 4) * 8 + g]);
+#pragma unroll
+    for (int p = 0; p < MAXP; ++p) {
+      if (2 * p < nblk) {
+        const float* q0 = st + (size_t)(2 * p) * BS;
+        const bool two = 2 * p + 1 < nblk;
+        const float* q1 = st + (size_t)(2 * p + 1) * BS;
+        const float a0 = q0[(r0 + t) * 8 + g], a2 = q0[(r0 + t + 4) * 8 + g];
+        const float a1 = two ? q1[(r0 + t) * 8 + g] : 0.f, a3 = two ? q1[(r0 + t + 4) * 8 + g] : 0.f;
+        mma3(acc[p], a0, a1, a2, a3, b);
+      }
+    }
+  }
+}
+
+// Reduce acc[p][4] over the 8 warps (fixed order) into partials: output index
+// out_of(block, a, c) for block < nblk.  red: 8 x MAXP x 32 x 4 doubles of shared memory.
+template <int MAXP, typename OutIdx>
+__device__ __forceinline__ void tc_reduce_xty(const float (&acc)[MAXP][4], int nblk, int warp, int lane,
+                                              double* red, double* partials, OutIdx out_of) {
+#pragma unroll
+  for (int p = 0; p < MAXP; ++p)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) red[((warp * MAXP + p) * 32 + lane) * 4 + u] = (double)acc[p][u];
+  __syncthreads();
+  for (int o = threadIdx.x; o < nblk * 64; o += blockDim.x) {
+    const int blk = o >> 6, a = (o >> 3) & 7, c = o & 7;
+    const int p = blk >> 1, m = a + 8 * (blk & 1);
+    const int ln = dfrag_lane(m, c), rg = dfrag_reg(m, c);
+    double sum = 0.0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) sum += red[((w * MAXP + p) * 32 + ln) * 4 + rg];
+    partials[out_of(blk, a, c)] = sum;
+  }
+}
+
+// H = Q^T W for nb <= 8 blocks
+__device__ __forceinline__ void tc_tproj(const int cta, const int ncta, int n, const float* Q, size_t bstride,
+                                         int nb, const float* W, double* partials) {
+  constexpr int TR = 128, BS = BlockStride<float>::value;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* stages = reinterpret_cast<float*>(smem_raw);
+  const int sstride = (nb + 1) * BS;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  float acc[4][4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[p][u] = 0.f;
+  const int ntiles = (n + TR - 1) / TR;
+  int tile = cta;
+  if (tile < ntiles) load_tile<float, TR>(stages, Q, bstride, nb, W, n, tile * TR);
+  cp_async_commit();
+  for (int it = 0; tile < ntiles; ++it, tile += ncta) {
+    const int next = tile + ncta;
+    if (next < ntiles) load_tile<float, TR>(stages + ((it + 1) & 1) * sstride, Q, bstride, nb, W, n, next * TR);
+    cp_async_commit();
+    cp_async_wait_1();
+    __syncthreads();
+    const float* st = stages + (it & 1) * sstride;
+    tc_accum_xty<4>(st, nb, st + (size_t)nb * BS, warp, g, t, acc);
+    __syncthreads();
+  }
+  cp_async_wait_0();
+  __syncthreads();
+  tc_reduce_xty<4>(acc, nb, warp, lane, reinterpret_cast<double*>(smem_raw), partials + (size_t)cta * PART_STRIDE,
+                   [](int blk, int a, int c) { return blk * 64 + a * 8 + c; });
+}
+
+// X = W - Q H (W overwritten, in shared memory and in global memory); then H2 = Q^T X and
+// G = X^T X.  H in Hs (nb x 64, FP32).
+__device__ __forceinline__ void tc_tupdate(const int cta, const int ncta, int n, const float* Q, size_t bstride,
+                                           int nb, float* W, const double* Hred, double* partials) {
+  constexpr int TR = 128, BS = BlockStride<float>::value;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* stages = reinterpret_cast<float*>(smem_raw);
+  const int sstride = (nb + 1) * BS;
+  float* Hs = stages + 2 * sstride;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  for (int u = threadIdx.x; u < nb * 64; u += blockDim.x) Hs[u] = (float)Hred[u];
+  float acc[5][4];
+#pragma unroll
+  for (int p = 0; p < 5; ++p)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[p][u] = 0.f;
+  const int ntiles = (n + TR - 1) / TR;
+  int tile = cta;
+  if (tile < ntiles) load_tile<float, TR>(stages, Q, bstride, nb, W, n, tile * TR);
+  cp_async_commit();
+  for (int it = 0; tile < ntiles; ++it, tile += ncta) {
+    const int next = tile + ncta;
+    if (next < ntiles) load_tile<float, TR>(stages + ((it + 1) & 1) * sstride, Q, bstride, nb, W, n, next * TR);
+    cp_async_commit();
+    cp_async_wait_1();
+    __syncthreads();
+    float* st = stages + (it & 1) * sstride;
+    float* Xs = st + (size_t)nb * BS;
+    // phase 1: rows 16 warp .. 16 warp + 15 of X = W - Q H
+    {
+      const int rb = 16 * warp;
+      float d[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int b = 0; b < nb; ++b) {
+        const float* q = st + (size_t)b * BS + (size_t)rb * 8;
+        const SplitB hb = split_b(Hs[b * 64 + t * 8 + g], Hs[b * 64 + (t + 4) * 8 + g]);
+        mma3(d, q[g * 8 + t], q[(g + 8) * 8 + t], q[g * 8 + t + 4], q[(g + 8) * 8 + t + 4], hb);
+      }
+      float* x0 = Xs + (size_t)(rb + g) * 8 + 2 * t;
+      float* x1 = Xs + (size_t)(rb + g + 8) * 8 + 2 * t;
+      const float v0 = x0[0] - d[0], v1 = x0[1] - d[1], v2 = x1[0] - d[2], v3 = x1[1] - d[3];
+      x0[0] = v0; x0[1] = v1; x1[0] = v2; x1[1] = v3;
+      const int row0 = tile * TR + rb + g, row1 = row0 + 8;
+      if (row0 < n) *reinterpret_cast<float2*>(W + (size_t)8 * row0 + 2 * t) = make_float2(v0, v1);
+      if (row1 < n) *reinterpret_cast<float2*>(W + (size_t)8 * row1 + 2 * t) = make_float2(v2, v3);
+    }
+    __syncthreads();
+    // phase 2: H2 = Q^T X and G = X^T X (X is block nb of the pair list; rows past n are 0)
+    tc_accum_xty<5>(st, nb + 1, Xs, warp, g, t, acc);
+    __syncthreads();
+  }
+  cp_async_wait_0();
+  __syncthreads();
+  tc_reduce_xty<5>(acc, nb + 1, warp, lane, reinterpret_cast<double*>(smem_raw), partials + (size_t)cta * PART_STRIDE,
+                   [nb](int blk, int a, int c) { return (blk < nb ? blk * 64 : 512) + a * 8 + c; });
+}
+
+// out = (W - Q H2) R^-1, deficient columns replaced (1: random, 2: zero)
+__device__ __forceinline__ void tc_tfinalize(const int cta, const int ncta, int n, const float* Q, size_t bstride,
+                                             int nb, const float* W, const double* H2red, const DevLanczos* lz,
+                                             float* out, uint64_t seed) {
+  constexpr int TR = 128, BS = BlockStride<float>::value;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* stages = reinterpret_cast<float*>(smem_raw);
+  const int sstride = (nb + 1) * BS;
+  float* Hs = stages + 2 * sstride;
+  float* Ri = Hs + 8 * 64;
+  __shared__ int dfc[8];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+  for (int u = tid; u < nb * 64; u += blockDim.x) Hs[u] = (float)H2red[u];
+  if (tid < 64) Ri[tid] = (float)lz->Rinv[tid];
+  if (tid < 8) dfc[tid] = lz->dcol[tid];
+  __syncthreads();
+  const SplitB rb0 = split_b(Ri[t * 8 + g], Ri[(t + 4) * 8 + g]);
+  const int ntiles = (n + TR - 1) / TR;
+  int tile = cta;
+  if (tile < ntiles) load_tile<float, TR>(stages, Q, bstride, nb, W, n, tile * TR);
+  cp_async_commit();
+  for (int it = 0; tile < ntiles; ++it, tile += ncta) {
+    const int next = tile + ncta;
+    if (next < ntiles) load_tile<float, TR>(stages + ((it + 1) & 1) * sstride, Q, bstride, nb, W, n, next * TR);
+    cp_async_commit();
+    cp_async_wait_1();
+    __syncthreads();
+    float* st = stages + (it & 1) * sstride;
+    float* Xs = st + (size_t)nb * BS;
+    const int rb = 16 * warp;
+    float d[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int b = 0; b < nb; ++b) {
+      const float* q = st + (size_t)b * BS + (size_t)rb * 8;
+      const SplitB hb = split_b(Hs[b * 64 + t * 8 + g], Hs[b * 64 + (t + 4) * 8 + g]);
+      mma3(d, q[g * 8 + t], q[(g + 8) * 8 + t], q[g * 8 + t + 4], q[(g + 8) * 8 + t + 4], hb);
+    }
+    // X = W - Q H2 back into this warp's own rows, then (X R^-1) as a second MMA
+    float* x0 = Xs + (size_t)(rb + g) * 8 + 2 * t;
+    float* x1 = Xs + (size_t)(rb + g + 8) * 8 + 2 * t;
+    x0[0] -= d[0]; x0[1] -= d[1]; x1[0] -= d[2]; x1[1] -= d[3];
+    __syncwarp();
+    const float* xr = Xs + (size_t)rb * 8;
+    float o[4] = {0.f, 0.f, 0.f, 0.f};
+    mma3(o, xr[g * 8 + t], xr[(g + 8) * 8 + t], xr[g * 8 + t + 4], xr[(g + 8) * 8 + t + 4], rb0);
+    const int row0 = tile * TR + rb + g, row1 = row0 + 8;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int row = u < 2 ? row0 : row1, a = 2 * t + (u & 1);
+      if (dfc[a] == 1) o[u] = (float)hash_uniform_o(seed, (uint64_t)row, (uint64_t)a);
+      else if (dfc[a] == 2) o[u] = 0.f;
+    }
+    if (row0 < n) *reinterpret_cast<float2*>(out + (size_t)8 * row0 + 2 * t) = make_float2(o[0], o[1]);
+    if (row1 < n) *reinterpret_cast<float2*>(out + (size_t)8 * row1 + 2 * t) = make_float2(o[2], o[3]);
+    __syncthreads();
+  }
+  cp_async_wait_0();
+}
+
+// out[o] = Q[:, :J] Y[:, 8o : 8o + 8] for o < nout <= 4; the residual block copied to
+// out[resid_slot] when resid is given.  Ys: J x 8 nout (FP32) in shared memory.
+__device__ __forceinline__ void tc_trestart(const int cta, const int ncta, int n, const float* Q, size_t bstride,
+                                            int nbk, int nout, const double* Y, float* out, size_t ostride,
+                                            const float* resid, int resid_slot) {
+  constexpr int TR = 128, BS = BlockStride<float>::value;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* stages = reinterpret_cast<float*>(smem_raw);
+  const int sstride = nbk * BS;
+  float* Ys = stages + 2 * sstride;
+  const int J = nbk * 8, ncol = nout * 8;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+  for (int u = tid; u < J * ncol; u += blockDim.x) Ys[u] = (float)Y[(u / ncol) * JMAX + (u % ncol)];
+  const int ntiles = (n + TR - 1) / TR;
+  int tile = cta;
+  if (tile < ntiles) load_tile<float, TR>(stages, Q, bstride, nbk, nullptr, n, tile * TR);
+  cp_async_commit();
+  for (int it = 0; tile < ntiles; ++it, tile += ncta) {
+    const int next = tile + ncta;
+    if (next < ntiles) load_tile<float, TR>(stages + ((it + 1) & 1) * sstride, Q, bstride, nbk, nullptr, n, next * TR);
+    cp_async_commit();
+    cp_async_wait_1();
+    __syncthreads();
+    const float* st = stages + (it & 1) * sstride;
+    const int rb = 16 * warp;
+    float d[4][4];
+#pragma unroll
+    for (int o = 0; o < 4; ++o)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) d[o][u] = 0.f;
+    for (int b = 0; b < nbk; ++b) {
+      const float* q = st + (size_t)b * BS + (size_t)rb * 8;
+      const float a0 = q[g * 8 + t], a1 = q[(g + 8) * 8 + t], a2 = q[g * 8 + t + 4], a3 = q[(g + 8) * 8 + t + 4];
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        if (o < nout) {
+          const SplitB yb = split_b(Ys[(b * 8 + t) * ncol + 8 * o + g], Ys[(b * 8 + t + 4) * ncol + 8 * o + g]);
+          mma3(d[o], a0, a1, a2, a3, yb);
+        }
+      }
+    }
+    const int row0 = tile * TR + rb + g, row1 = row0 + 8;
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+      if (o < nout) {
+        if (row0 < n) *reinterpret_cast<float2*>(out + o * ostride + (size_t)8 * row0 + 2 * t) = make_float2(d[o][0], d[o][1]);
+        if (row1 < n) *reinterpret_cast<float2*>(out + o * ostride + (size_t)8 * row1 + 2 * t) = make_float2(d[o][2], d[o][3]);
+      }
+    }
+    if (resid) {
+      for (int p = tid; p < TR * 8; p += blockDim.x) {
+        const int row = tile * TR + p / 8;
+        if (row < n) out[resid_slot * ostride + (size_t)8 * row + (p % 8)] = resid[(size_t)8 * row + (p % 8)];
+      }
+    }
+    __syncthreads();
+  }
+  cp_async_wait_0();
+}
+
 // ---- H = Q^T W --------------------------------------------------------------------------
 // Items (b, a-pair): 4 nb <= 32.  256 threads = 8 row groups (warps) x 32 slots.  A slot
 // owns one item, 2 basis columns x all 8 columns of W (16 accumulators, 3 shared loads
@@ -120,6 +437,11 @@ template <typename T>
 __device__ __forceinline__ void k_tproj_dev(const int cta, const int ncta, int n, const T* USBS_RESTRICT Q, size_t bstride, int nb,
                                                const T* USBS_RESTRICT W, double* USBS_RESTRICT partials,
                                                const int* USBS_RESTRICT mask) {
+  if constexpr (sizeof(T) == 4) {
+    if (mask && *mask == 0) return;
+    tc_tproj(cta, ncta, n, Q, bstride, nb, W, partials);
+    return;
+  }
   if (mask && *mask == 0) return;
   constexpr int TR = TileRows<T>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -171,6 +493,11 @@ __device__ __forceinline__ void k_tupdate_dev(const int cta, const int ncta, int
                                                  T* USBS_RESTRICT W, const double* USBS_RESTRICT Hred,
                                                  double* USBS_RESTRICT partials,
                                                  const int* USBS_RESTRICT mask) {
+  if constexpr (sizeof(T) == 4) {
+    if (mask && *mask == 0) return;
+    tc_tupdate(cta, ncta, n, Q, bstride, nb, W, Hred, partials);
+    return;
+  }
   if (mask && *mask == 0) return;
   constexpr int TR = TileRows<T>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -261,20 +588,16 @@ __device__ __forceinline__ void k_tupdate_dev(const int cta, const int ncta, int
   }
 }
 
-// ---- out = (W - Q H2) R^-1; deficient columns replaced by random vectors -----------------------
-__device__ __forceinline__ double hash_uniform_o(uint64_t seed, uint64_t row, uint64_t col) {
-  uint64_t z = seed + 0x9E3779B97F4A7C15ull * (row * 16 + col + 1);
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  z = z ^ (z >> 31);
-  return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
-}
-
 template <typename T>
 __device__ __forceinline__ void k_tfinalize_dev(const int cta, const int ncta, int n, const T* USBS_RESTRICT Q, size_t bstride,
                                                    int nb, const T* W, const double* USBS_RESTRICT H2red,
                                                    const DevLanczos* USBS_RESTRICT lz, T* out,
                                                    const int* USBS_RESTRICT mask, uint64_t seed) {
+  if constexpr (sizeof(T) == 4) {
+    if (mask && *mask == 0) return;
+    tc_tfinalize(cta, ncta, n, Q, bstride, nb, W, H2red, lz, out, seed);
+    return;
+  }
   if (mask && *mask == 0) return;
   constexpr int TR = TileRows<T>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -349,6 +672,10 @@ __device__ __forceinline__ void k_trestart_dev(const int cta, const int ncta, in
                                                   int nout, const double* USBS_RESTRICT Y,
                                                   T* USBS_RESTRICT out, size_t ostride,
                                                   const T* USBS_RESTRICT resid, int resid_slot) {
+  if constexpr (sizeof(T) == 4) {
+    tc_trestart(cta, ncta, n, Q, bstride, nbk, nout, Y, out, ostride, resid, resid_slot);
+    return;
+  }
   constexpr int TR = TileRows<T>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* stages = reinterpret_cast<T*>(smem_raw);

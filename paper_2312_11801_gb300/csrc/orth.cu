@@ -106,7 +106,7 @@ template <typename T>
 int Orth<T>::proj(Ctx* c, const void* Qb, int nb, const void* W, const int* mask) {
   USBS_LAUNCH_B(c, USBS_KIND_REORTH, mask ? 0.0 : 8.0 * sizeof(T) * c->n * (nb + 1));
   set_attrs<T>();
-  // the epilogue reuses the stage buffers for 8 x 32 x 16 FP64 partial sums
+  // the epilogue reuses the stage buffers for 8 x 32 x 16 FP64 partial sums (= tc_red_bytes(4))
   const size_t sm = std::max(tile_smem<T>(nb, 0), sizeof(double) * 8 * 512);
   const int g = orth_grid(c, c->n, (const void*)k_tproj<T>, sm);
   k_tproj<T><<<g, 256, sm, c->stream>>>((int)c->n, (const T*)Qb, (size_t)c->n * 8, nb, (const T*)W,
@@ -129,9 +129,11 @@ template <typename T>
 int Orth<T>::update(Ctx* c, const void* Qb, int nb, void* W, const int* mask) {
   USBS_LAUNCH_B(c, USBS_KIND_REORTH_UPDATE, mask ? 0.0 : 8.0 * sizeof(T) * c->n * (nb + 2));
   set_attrs<T>();
-  // the epilogue reuses the stage buffers for 8 x (32 or 64) x 16 FP64 partial sums
-  const size_t sm = std::max(tile_smem<T>(nb, 8 * 64),
-                             sizeof(double) * 8 * (4 * (nb + 1) <= 32 ? 32 : 64) * 16);
+  // the epilogue reuses the stage buffers for its FP64 warp partials: FP32 (tensor cores)
+  // 8 warps x 5 pairs x 32 x 4; FP64 8 warps x (32 or 64) slots x 16
+  const size_t red = sizeof(T) == 4 ? tc_red_bytes(5)
+                                    : sizeof(double) * 8 * (4 * (nb + 1) <= 32 ? 32 : 64) * 16;
+  const size_t sm = std::max(tile_smem<T>(nb, 8 * 64), red);
   const int g = orth_grid(c, c->n, (const void*)k_tupdate<T>, sm);
   k_tupdate<T><<<g, 256, sm, c->stream>>>((int)c->n, (const T*)Qb, (size_t)c->n * 8, nb, (T*)W,
                                           c->red + RED_H, c->partials, mask);
