@@ -139,8 +139,14 @@ __device__ __forceinline__ void mma3(float (&d)[4], float a0, float a1, float a2
 }
 
 // shared memory of the warp reduction of tc_reduce_xty with MAXP pairs: 8 x MAXP x 32 x 4
-// doubles (tproj: 4 pairs, 32 KB; tupdate: 5 pairs, 40 KB)
-constexpr size_t tc_red_bytes(int maxp) { return sizeof(double) * 8 * (size_t)maxp * 32 * 4; }
+// floats (tproj: 4 pairs, 16 KB; tupdate: 5 pairs, 20 KB)
+constexpr size_t tc_red_bytes(int maxp) { return sizeof(float) * 8 * (size_t)maxp * 32 * 4; }
+
+// D += A B in plain TF32 (one MMA): for the first Gram-Schmidt projection, whose rounding
+// the second pass removes (H2 = Q^T (W - Q H) = H_exact - H when the update is exact)
+__device__ __forceinline__ void mma1(float (&d)[4], float a0, float a1, float a2, float a3, float b0, float b1) {
+  mma_tf32(d, tf32_of(a0), tf32_of(a1), tf32_of(a2), tf32_of(a3), tf32_of(b0), tf32_of(b1));
+}
 
 // index of output (m, c) of a 16 x 8 D fragment: lane and register
 __device__ __forceinline__ int dfrag_lane(int m, int c) { return (m & 7) * 4 + (c >> 1); }
@@ -150,49 +156,56 @@ __device__ __forceinline__ int dfrag_reg(int m, int c) { return ((m >> 3) << 1) 
 // offset i * BS; block nblk-1 may be Y itself), accumulated per block pair in acc: pair p
 // covers blocks 2p and 2p+1 (rows m 0..7 and 8..15 of the MMA).  Warp w takes the 8-row
 // k-steps w and w + 8 of the 128-row tile.
-template <int MAXP>
+template <int MAXP, bool SPLIT>
 __device__ __forceinline__ void tc_accum_xty(const float* st, int nblk, const float* Y, int warp, int g, int t,
                                              float (&acc)[MAXP][4]) {
   constexpr int BS = BlockStride<float>::value;
-  for (int ks = warp; ks < 16; ks += 8) {
-    const int r0 = ks * 8;
-    const SplitB b = split_b(Y[(r0 + t) * 8 + g], Y[(r0 + t + 4) * 8 + g]);
+  const int off = t * 8 + g;   // element (row t, column g) of an 8-row step; + 32 for row t + 4
+#pragma unroll
+  for (int kk = 0; kk < 2; ++kk) {
+    const int r0 = (warp + 8 * kk) * 8;
+    const float* y = Y + r0 * 8 + off;
+    const float b0 = y[0], b1 = y[32];
+    SplitB b;
+    if (SPLIT) b = split_b(b0, b1);
 #pragma unroll
     for (int p = 0; p < MAXP; ++p) {
       if (2 * p < nblk) {
-        const float* q0 = st + (size_t)(2 * p) * BS;
+        const float* q0 = st + (size_t)(2 * p) * BS + r0 * 8 + off;
         const bool two = 2 * p + 1 < nblk;
-        const float* q1 = st + (size_t)(2 * p + 1) * BS;
-        const float a0 = q0[(r0 + t) * 8 + g], a2 = q0[(r0 + t + 4) * 8 + g];
-        const float a1 = two ? q1[(r0 + t) * 8 + g] : 0.f, a3 = two ? q1[(r0 + t + 4) * 8 + g] : 0.f;
-        mma3(acc[p], a0, a1, a2, a3, b);
+        const float a0 = q0[0], a2 = q0[32];
+        const float a1 = two ? q0[BS] : 0.f, a3 = two ? q0[BS + 32] : 0.f;
+        if (SPLIT) mma3(acc[p], a0, a1, a2, a3, b);
+        else mma1(acc[p], a0, a1, a2, a3, b0, b1);
       }
     }
   }
 }
 
-// Reduce acc[p][4] over the 8 warps (fixed order) into partials: output index
-// out_of(block, a, c) for block < nblk.  red: 8 x MAXP x 32 x 4 doubles of shared memory.
+// Reduce acc[p][4] over the 8 warps (fixed order, FP32 like the sums inside a CTA) into
+// the CTA's FP64 partials: output index out_of(block, a, c) for block < nblk.
+// red: 8 x MAXP x 32 x 4 floats of shared memory.
 template <int MAXP, typename OutIdx>
 __device__ __forceinline__ void tc_reduce_xty(const float (&acc)[MAXP][4], int nblk, int warp, int lane,
-                                              double* red, double* partials, OutIdx out_of) {
+                                              float* red, double* partials, OutIdx out_of) {
 #pragma unroll
   for (int p = 0; p < MAXP; ++p)
-#pragma unroll
-    for (int u = 0; u < 4; ++u) red[((warp * MAXP + p) * 32 + lane) * 4 + u] = (double)acc[p][u];
+    *reinterpret_cast<float4*>(red + ((warp * MAXP + p) * 32 + lane) * 4) =
+        make_float4(acc[p][0], acc[p][1], acc[p][2], acc[p][3]);
   __syncthreads();
   for (int o = threadIdx.x; o < nblk * 64; o += blockDim.x) {
     const int blk = o >> 6, a = (o >> 3) & 7, c = o & 7;
     const int p = blk >> 1, m = a + 8 * (blk & 1);
     const int ln = dfrag_lane(m, c), rg = dfrag_reg(m, c);
-    double sum = 0.0;
+    float sum = 0.f;
 #pragma unroll
     for (int w = 0; w < 8; ++w) sum += red[((w * MAXP + p) * 32 + ln) * 4 + rg];
-    partials[out_of(blk, a, c)] = sum;
+    partials[out_of(blk, a, c)] = (double)sum;
   }
 }
 
-// H = Q^T W for nb <= 8 blocks
+// H = Q^T W for nb <= 8 blocks, plain TF32 (the second pass of the block Gram-Schmidt
+// removes its rounding from both the new block and the projected matrix)
 __device__ __forceinline__ void tc_tproj(const int cta, const int ncta, int n, const float* Q, size_t bstride,
                                          int nb, const float* W, double* partials) {
   constexpr int TR = 128, BS = BlockStride<float>::value;
@@ -216,12 +229,12 @@ __device__ __forceinline__ void tc_tproj(const int cta, const int ncta, int n, c
     cp_async_wait_1();
     __syncthreads();
     const float* st = stages + (it & 1) * sstride;
-    tc_accum_xty<4>(st, nb, st + (size_t)nb * BS, warp, g, t, acc);
+    tc_accum_xty<4, false>(st, nb, st + (size_t)nb * BS, warp, g, t, acc);
     __syncthreads();
   }
   cp_async_wait_0();
   __syncthreads();
-  tc_reduce_xty<4>(acc, nb, warp, lane, reinterpret_cast<double*>(smem_raw), partials + (size_t)cta * PART_STRIDE,
+  tc_reduce_xty<4>(acc, nb, warp, lane, reinterpret_cast<float*>(smem_raw), partials + (size_t)cta * PART_STRIDE,
                    [](int blk, int a, int c) { return blk * 64 + a * 8 + c; });
 }
 
@@ -272,12 +285,12 @@ __device__ __forceinline__ void tc_tupdate(const int cta, const int ncta, int n,
     }
     __syncthreads();
     // phase 2: H2 = Q^T X and G = X^T X (X is block nb of the pair list; rows past n are 0)
-    tc_accum_xty<5>(st, nb + 1, Xs, warp, g, t, acc);
+    tc_accum_xty<5, true>(st, nb + 1, Xs, warp, g, t, acc);
     __syncthreads();
   }
   cp_async_wait_0();
   __syncthreads();
-  tc_reduce_xty<5>(acc, nb + 1, warp, lane, reinterpret_cast<double*>(smem_raw), partials + (size_t)cta * PART_STRIDE,
+  tc_reduce_xty<5>(acc, nb + 1, warp, lane, reinterpret_cast<float*>(smem_raw), partials + (size_t)cta * PART_STRIDE,
                    [nb](int blk, int a, int c) { return (blk < nb ? blk * 64 : 512) + a * 8 + c; });
 }
 

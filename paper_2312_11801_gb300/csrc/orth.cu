@@ -97,7 +97,10 @@ static int resident_ctas(const void* kernel, size_t smem) {
 int orth_grid(Ctx* c, int64_t rows, const void* kernel, size_t smem) {
   const int TR = c->fp64 ? TileRows<double>::value : TileRows<float>::value;
   int64_t g = (rows + TR - 1) / TR;
-  const int64_t cap = std::min<int64_t>(c->max_parts, (int64_t)resident_ctas(kernel, smem) * c->num_sms);
+  // at most 2 CTAs per SM: the tiles are issue-bound, more CTAs only lengthen the
+  // reduction of their partials
+  const int per_sm = std::min(resident_ctas(kernel, smem), 2);
+  const int64_t cap = std::min<int64_t>(c->max_parts, (int64_t)per_sm * c->num_sms);
   if (g > cap) g = cap;
   return (int)(g < 1 ? 1 : g);
 }
