@@ -81,30 +81,30 @@ __device__ void b_orth_block(BatchCtx<T>& b, T* Q, int nb, T* W, T* out, int j, 
   double* red = d->red;
   const double thr = sizeof(T) == 8 ? 1e-16 : 1e-6;
   if (nb > 0) {
-    k_tproj_dev<T>(0, 1, d->n, Q, bs, nb, W, red + RED_H, nullptr);
+    k_tproj_dev<T>(0, 1, d->n, Q, bs, nb, W, red + RED_H, nullptr, &d->lz->status);
     __syncthreads();
   }
-  k_tupdate_dev<T>(0, 1, d->n, Q, bs, nb, W, red + RED_H, red + RED_H2, nullptr);
+  k_tupdate_dev<T>(0, 1, d->n, Q, bs, nb, W, red + RED_H, red + RED_H2, nullptr, &d->lz->status);
   __syncthreads();
   k_chol_block_dev(d->lz, red, j, nb, write_T, is_resid, 0, thr);
   __syncthreads();
   k_tfinalize_dev<T>(0, 1, d->n, Q, bs, nb, W, red + RED_H2, d->lz, out, nullptr,
-                     d->seed + 0x1000003ull * (b.rng++));
+                     d->seed + 0x1000003ull * (b.rng++), &d->lz->status);
   __syncthreads();
   const int* defl = &d->lz->defl;
   const int* defl2 = &d->lz->defl2;
   for (int pass = 1; pass <= 2; ++pass) {
     const int* mask = pass == 1 ? defl : defl2;
     if (nb > 0) {
-      k_tproj_dev<T>(0, 1, d->n, Q, bs, nb, out, red + RED_H, mask);
+      k_tproj_dev<T>(0, 1, d->n, Q, bs, nb, out, red + RED_H, mask, &d->lz->status);
       __syncthreads();
     }
-    k_tupdate_dev<T>(0, 1, d->n, Q, bs, nb, out, red + RED_H, red + RED_H2, mask);
+    k_tupdate_dev<T>(0, 1, d->n, Q, bs, nb, out, red + RED_H, red + RED_H2, mask, &d->lz->status);
     __syncthreads();
     k_chol_block_dev(d->lz, red, j, nb, 0, is_resid, pass, thr);
     __syncthreads();
     k_tfinalize_dev<T>(0, 1, d->n, Q, bs, nb, out, red + RED_H2, d->lz, out, mask,
-                       d->seed + 0x2000011ull * (b.rng++));
+                       d->seed + 0x2000011ull * (b.rng++), &d->lz->status);
     __syncthreads();
   }
 }
@@ -142,9 +142,9 @@ __device__ int b_lanczos(BatchCtx<T>& b, const double* y, const T* start, T* out
     }
     k_ritz_dev<S, J>(d->lz, d->kc, d->lanczos_tol, sweeps, jac_eps);
     __syncthreads();
-    if (d->lz->status != 0) { rc = USBS_ENUMERIC; break; }
+    if (d->lz->status != 0) { rc = d->lz->status == USBS_ETIMEOUT ? USBS_ETIMEOUT : USBS_ENUMERIC; break; }
     if (d->lz->converged || cycle == d->restarts - 1) break;
-    k_trestart_dev<T>(0, 1, n, Q, bs, nblk, keep / 8, d->lz->Y, Q2, bs, Q + nblk * bs, keep / 8);
+    k_trestart_dev<T>(0, 1, n, Q, bs, nblk, keep / 8, d->lz->Y, Q2, bs, Q + nblk * bs, keep / 8, &d->lz->status);
     __syncthreads();
     T* t = Q; Q = Q2; Q2 = t;
     nb0 = keep / 8;
@@ -152,7 +152,7 @@ __device__ int b_lanczos(BatchCtx<T>& b, const double* y, const T* start, T* out
   b.Q = Q;
   b.Q2 = Q2;
   if (rc == 0) {
-    k_trestart_dev<T>(0, 1, n, Q, bs, nblk, 1, d->lz->Y, out_vecs, bs, nullptr, 0);
+    k_trestart_dev<T>(0, 1, n, Q, bs, nblk, 1, d->lz->Y, out_vecs, bs, nullptr, 0, &d->lz->status);
     __syncthreads();
   }
   return rc;
@@ -169,7 +169,7 @@ __device__ int b_step(BatchCtx<T>& b, T*& V, T*& Vnew, double*& ax, double*& axn
   // V^T C V
   k_spmm_dev<T>(0, 1, n, d->rowptr, d->col, (const T*)d->valC, (const T*)d->dC, V, (T*)d->W);
   __syncthreads();
-  k_tproj_dev<T>(0, 1, n, V, (size_t)n * 8, 1, (const T*)d->W, red + RED_VC, nullptr);
+  k_tproj_dev<T>(0, 1, n, V, (size_t)n * 8, 1, (const T*)d->W, red + RED_VC, nullptr, &d->lz->status);
   __syncthreads();
   // [G | A Xbar | y - b/rho]^T [G | A Xbar | y - b/rho]
   k_gstats_dev<T>(0, 1, m, d->con_ptr, d->ent_i, d->ent_j, (const T*)d->ent_v, V, ax, d->y, d->b,

@@ -54,33 +54,7 @@ template <> __device__ __forceinline__ void sts4<double>(double* p, const double
   reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
 }
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
-  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  const int src_bytes = valid ? 16 : 0;   // 0: fill the 16 bytes with zeros
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::); }
-__device__ __forceinline__ void cp_async_wait_0() { asm volatile("cp.async.wait_group 0;\n" ::); }
 
-// Copy rows [row0, row0 + TR) of blocks 0..nq-1 of Q (and of W if W != nullptr, placed
-// after them) into one stage: block blk at blk * BlockStride, row r at r * 8 within it.
-template <typename T, int TR>
-__device__ __forceinline__ void load_tile(T* stage, const T* USBS_RESTRICT Q, size_t bstride, int nq,
-                                          const T* USBS_RESTRICT W, int n, int row0) {
-  constexpr int CH = 8 * sizeof(T) / 16;           // 16-byte chunks per row
-  const int nblk = nq + (W ? 1 : 0);
-  const int total = nblk * TR * CH;
-  for (int u = threadIdx.x; u < total; u += blockDim.x) {
-    const int b = u / (TR * CH);
-    const int rem = u % (TR * CH);
-    const int r = rem / CH, ch = rem % CH;
-    const int row = row0 + r;
-    const bool valid = row < n;
-    const T* src = (b < nq ? Q + b * bstride : W) + (size_t)8 * (valid ? row : 0) + ch * (16 / sizeof(T));
-    cp_async16(stage + (size_t)b * BlockStride<T>::value + (size_t)r * 8 + ch * (16 / sizeof(T)), src, valid);
-  }
-}
 
 // ---- out = (W - Q H2) R^-1; deficient columns replaced by random vectors -----------------------
 __device__ __forceinline__ double hash_uniform_o(uint64_t seed, uint64_t row, uint64_t col) {
@@ -91,6 +65,104 @@ __device__ __forceinline__ double hash_uniform_o(uint64_t seed, uint64_t row, ui
   return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
 }
 
+
+
+// ---- TMA staging of tiles ------------------------------------------------------------------
+// The tile of one block (rows row0 .. row0 + TR - 1, 8 values each) is contiguous in the
+// block-major layout, so one bulk asynchronous copy (cp.async.bulk) moves it; one thread
+// issues the copies of a tile and an mbarrier with a transaction count tells the CTA when
+// they have landed.  Rows past n are not copied: the threads zero them in shared memory.
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(smem_u32(bar)));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Two stage barriers, initialised by thread 0 and published by the barrier that follows.
+__device__ __forceinline__ void tiles_begin(uint64_t* bar) {
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+}
+
+// Stage rows [row0, row0 + TR) of blocks 0..nq-1 of Q and of W (if given, after them).
+template <typename T, int TR>
+__device__ __forceinline__ void tile_load(T* stage, const T* Q, size_t bstride, int nq, const T* W, int n,
+                                          int row0, uint64_t* bar) {
+  constexpr int BS = BlockStride<T>::value;
+  const int valid = min(TR, n - row0);
+  const int nblk = nq + (W ? 1 : 0);
+  if (valid < TR) {
+    const int per = (TR - valid) * 8;
+    for (int u = threadIdx.x; u < nblk * per; u += blockDim.x) {
+      const int b = u / per, rem = u % per;
+      stage[(size_t)b * BS + (size_t)valid * 8 + rem] = (T)0;
+    }
+  }
+  if (threadIdx.x == 0) {
+    const unsigned bytes = (unsigned)valid * 8u * (unsigned)sizeof(T);
+    // the stage may hold generic stores of the previous tile
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    mbar_expect_tx(bar, bytes * (unsigned)nblk);
+    for (int b = 0; b < nblk; ++b) {
+      const T* src = (b < nq ? Q + b * bstride : W) + (size_t)8 * row0;
+      bulk_g2s(stage + (size_t)b * BS, src, bytes, bar);
+    }
+  }
+}
+
+// Wait for the copies of one stage: at most 2^20 polls with a short sleep (about 0.1 s);
+// false, with USBS_ETIMEOUT in *status, if they did not land.
+__device__ __forceinline__ bool tile_wait(uint64_t* bar, unsigned parity, int* status) {
+  for (int k = 0; k < (1 << 20); ++k) {
+    if (mbar_test(bar, parity)) return true;
+    __nanosleep(64);
+  }
+  if (status) atomicExch(status, USBS_ETIMEOUT);
+  return false;
+}
+
+// After the tile loop: on an abort, wait (bounded) for copies that may still be landing in
+// either stage, then release the barriers.
+__device__ __forceinline__ void tiles_end(uint64_t* bar, bool aborted, int it_abort, int left_after, int* status) {
+  (void)status;
+  if (aborted) {
+    tile_wait(&bar[it_abort & 1], (it_abort >> 1) & 1, nullptr);
+    if (left_after) tile_wait(&bar[(it_abort + 1) & 1], ((it_abort + 1) >> 1) & 1, nullptr);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_inval(&bar[0]);
+    mbar_inval(&bar[1]);
+  }
+}
 
 // =============================================================================================
 // FP32 bodies on the tensor cores.  Every contraction of the tiles is an m16n8k8 TF32 MMA
@@ -142,12 +214,6 @@ __device__ __forceinline__ void mma3(float (&d)[4], float a0, float a1, float a2
 // floats (tproj: 4 pairs, 16 KB; tupdate: 5 pairs, 20 KB)
 constexpr size_t tc_red_bytes(int maxp) { return sizeof(float) * 8 * (size_t)maxp * 32 * 4; }
 
-// D += A B in plain TF32 (one MMA): for the first Gram-Schmidt projection, whose rounding
-// the second pass removes (H2 = Q^T (W - Q H) = H_exact - H when the update is exact)
-__device__ __forceinline__ void mma1(float (&d)[4], float a0, float a1, float a2, float a3, float b0, float b1) {
-  mma_tf32(d, tf32_of(a0), tf32_of(a1), tf32_of(a2), tf32_of(a3), tf32_of(b0), tf32_of(b1));
-}
-
 // index of output (m, c) of a 16 x 8 D fragment: lane and register
 __device__ __forceinline__ int dfrag_lane(int m, int c) { return (m & 7) * 4 + (c >> 1); }
 __device__ __forceinline__ int dfrag_reg(int m, int c) { return ((m >> 3) << 1) | (c & 1); }
@@ -156,7 +222,7 @@ __device__ __forceinline__ int dfrag_reg(int m, int c) { return ((m >> 3) << 1) 
 // offset i * BS; block nblk-1 may be Y itself), accumulated per block pair in acc: pair p
 // covers blocks 2p and 2p+1 (rows m 0..7 and 8..15 of the MMA).  Warp w takes the 8-row
 // k-steps w and w + 8 of the 128-row tile.
-template <int MAXP, bool SPLIT>
+template <int MAXP>
 __device__ __forceinline__ void tc_accum_xty(const float* st, int nblk, const float* Y, int warp, int g, int t,
                                              float (&acc)[MAXP][4]) {
   constexpr int BS = BlockStride<float>::value;
@@ -165,9 +231,7 @@ __device__ __forceinline__ void tc_accum_xty(const float* st, int nblk, const fl
   for (int kk = 0; kk < 2; ++kk) {
     const int r0 = (warp + 8 * kk) * 8;
     const float* y = Y + r0 * 8 + off;
-    const float b0 = y[0], b1 = y[32];
-    SplitB b;
-    if (SPLIT) b = split_b(b0, b1);
+    const SplitB b = split_b(y[0], y[32]);
 #pragma unroll
     for (int p = 0; p < MAXP; ++p) {
       if (2 * p < nblk) {
@@ -175,8 +239,7 @@ __device__ __forceinline__ void tc_accum_xty(const float* st, int nblk, const fl
         const bool two = 2 * p + 1 < nblk;
         const float a0 = q0[0], a2 = q0[32];
         const float a1 = two ? q0[BS] : 0.f, a3 = two ? q0[BS + 32] : 0.f;
-        if (SPLIT) mma3(acc[p], a0, a1, a2, a3, b);
-        else mma1(acc[p], a0, a1, a2, a3, b0, b1);
+        mma3(acc[p], a0, a1, a2, a3, b);
       }
     }
   }
@@ -204,10 +267,9 @@ __device__ __forceinline__ void tc_reduce_xty(const float (&acc)[MAXP][4], int n
   }
 }
 
-// H = Q^T W for nb <= 8 blocks, plain TF32 (the second pass of the block Gram-Schmidt
-// removes its rounding from both the new block and the projected matrix)
+// H = Q^T W for nb <= 8 blocks
 __device__ __forceinline__ void tc_tproj(const int cta, const int ncta, int n, const float* Q, size_t bstride,
-                                         int nb, const float* W, double* partials) {
+                                         int nb, const float* W, double* partials, int* status) {
   constexpr int TR = 128, BS = BlockStride<float>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* stages = reinterpret_cast<float*>(smem_raw);
@@ -220,19 +282,25 @@ __device__ __forceinline__ void tc_tproj(const int cta, const int ncta, int n, c
     for (int u = 0; u < 4; ++u) acc[p][u] = 0.f;
   const int ntiles = (n + TR - 1) / TR;
   int tile = cta;
-  if (tile < ntiles) load_tile<float, TR>(stages, Q, bstride, nb, W, n, tile * TR);
-  cp_async_commit();
+  __shared__ uint64_t tbar[2];
+  tiles_begin(tbar);
+  bool aborted = false;
+  int it_abort = 0, left_after = 0;
+  if (tile < ntiles) tile_load<float, TR>(stages, Q, bstride, nb, W, n, tile * TR, &tbar[0]);
   for (int it = 0; tile < ntiles; ++it, tile += ncta) {
     const int next = tile + ncta;
-    if (next < ntiles) load_tile<float, TR>(stages + ((it + 1) & 1) * sstride, Q, bstride, nb, W, n, next * TR);
-    cp_async_commit();
-    cp_async_wait_1();
-    __syncthreads();
+    if (next < ntiles) tile_load<float, TR>(stages + ((it + 1) & 1) * sstride, Q, bstride, nb, W, n, next * TR, &tbar[(it + 1) & 1]);
+    if (!__syncthreads_and(tile_wait(&tbar[it & 1], (it >> 1) & 1, status))) {
+      aborted = true;
+      it_abort = it;
+      left_after = next < ntiles;
+      break;
+    }
     const float* st = stages + (it & 1) * sstride;
-    tc_accum_xty<4, false>(st, nb, st + (size_t)nb * BS, warp, g, t, acc);
+    tc_accum_xty<4>(st, nb, st + (size_t)nb * BS, warp, g, t, acc);
     __syncthreads();
   }
-  cp_async_wait_0();
+  tiles_end(tbar, aborted, it_abort, left_after, status);
   __syncthreads();
   tc_reduce_xty<4>(acc, nb, warp, lane, reinterpret_cast<float*>(smem_raw), partials + (size_t)cta * PART_STRIDE,
                    [](int blk, int a, int c) { return blk * 64 + a * 8 + c; });
@@ -241,7 +309,7 @@ __device__ __forceinline__ void tc_tproj(const int cta, const int ncta, int n, c
 // X = W - Q H (W overwritten, in shared memory and in global memory); then H2 = Q^T X and
 // G = X^T X.  H in Hs (nb x 64, FP32).
 __device__ __forceinline__ void tc_tupdate(const int cta, const int ncta, int n, const float* Q, size_t bstride,
-                                           int nb, float* W, const double* Hred, double* partials) {
+                                           int nb, float* W, const double* Hred, double* partials, int* status) {
   constexpr int TR = 128, BS = BlockStride<float>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* stages = reinterpret_cast<float*>(smem_raw);
@@ -256,14 +324,20 @@ __device__ __forceinline__ void tc_tupdate(const int cta, const int ncta, int n,
     for (int u = 0; u < 4; ++u) acc[p][u] = 0.f;
   const int ntiles = (n + TR - 1) / TR;
   int tile = cta;
-  if (tile < ntiles) load_tile<float, TR>(stages, Q, bstride, nb, W, n, tile * TR);
-  cp_async_commit();
+  __shared__ uint64_t tbar[2];
+  tiles_begin(tbar);
+  bool aborted = false;
+  int it_abort = 0, left_after = 0;
+  if (tile < ntiles) tile_load<float, TR>(stages, Q, bstride, nb, W, n, tile * TR, &tbar[0]);
   for (int it = 0; tile < ntiles; ++it, tile += ncta) {
     const int next = tile + ncta;
-    if (next < ntiles) load_tile<float, TR>(stages + ((it + 1) & 1) * sstride, Q, bstride, nb, W, n, next * TR);
-    cp_async_commit();
-    cp_async_wait_1();
-    __syncthreads();
+    if (next < ntiles) tile_load<float, TR>(stages + ((it + 1) & 1) * sstride, Q, bstride, nb, W, n, next * TR, &tbar[(it + 1) & 1]);
+    if (!__syncthreads_and(tile_wait(&tbar[it & 1], (it >> 1) & 1, status))) {
+      aborted = true;
+      it_abort = it;
+      left_after = next < ntiles;
+      break;
+    }
     float* st = stages + (it & 1) * sstride;
     float* Xs = st + (size_t)nb * BS;
     // phase 1: rows 16 warp .. 16 warp + 15 of X = W - Q H
@@ -285,10 +359,10 @@ __device__ __forceinline__ void tc_tupdate(const int cta, const int ncta, int n,
     }
     __syncthreads();
     // phase 2: H2 = Q^T X and G = X^T X (X is block nb of the pair list; rows past n are 0)
-    tc_accum_xty<5, true>(st, nb + 1, Xs, warp, g, t, acc);
+    tc_accum_xty<5>(st, nb + 1, Xs, warp, g, t, acc);
     __syncthreads();
   }
-  cp_async_wait_0();
+  tiles_end(tbar, aborted, it_abort, left_after, status);
   __syncthreads();
   tc_reduce_xty<5>(acc, nb + 1, warp, lane, reinterpret_cast<float*>(smem_raw), partials + (size_t)cta * PART_STRIDE,
                    [nb](int blk, int a, int c) { return (blk < nb ? blk * 64 : 512) + a * 8 + c; });
@@ -297,7 +371,7 @@ __device__ __forceinline__ void tc_tupdate(const int cta, const int ncta, int n,
 // out = (W - Q H2) R^-1, deficient columns replaced (1: random, 2: zero)
 __device__ __forceinline__ void tc_tfinalize(const int cta, const int ncta, int n, const float* Q, size_t bstride,
                                              int nb, const float* W, const double* H2red, const DevLanczos* lz,
-                                             float* out, uint64_t seed) {
+                                             float* out, uint64_t seed, int* status) {
   constexpr int TR = 128, BS = BlockStride<float>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* stages = reinterpret_cast<float*>(smem_raw);
@@ -313,14 +387,20 @@ __device__ __forceinline__ void tc_tfinalize(const int cta, const int ncta, int 
   const SplitB rb0 = split_b(Ri[t * 8 + g], Ri[(t + 4) * 8 + g]);
   const int ntiles = (n + TR - 1) / TR;
   int tile = cta;
-  if (tile < ntiles) load_tile<float, TR>(stages, Q, bstride, nb, W, n, tile * TR);
-  cp_async_commit();
+  __shared__ uint64_t tbar[2];
+  tiles_begin(tbar);
+  bool aborted = false;
+  int it_abort = 0, left_after = 0;
+  if (tile < ntiles) tile_load<float, TR>(stages, Q, bstride, nb, W, n, tile * TR, &tbar[0]);
   for (int it = 0; tile < ntiles; ++it, tile += ncta) {
     const int next = tile + ncta;
-    if (next < ntiles) load_tile<float, TR>(stages + ((it + 1) & 1) * sstride, Q, bstride, nb, W, n, next * TR);
-    cp_async_commit();
-    cp_async_wait_1();
-    __syncthreads();
+    if (next < ntiles) tile_load<float, TR>(stages + ((it + 1) & 1) * sstride, Q, bstride, nb, W, n, next * TR, &tbar[(it + 1) & 1]);
+    if (!__syncthreads_and(tile_wait(&tbar[it & 1], (it >> 1) & 1, status))) {
+      aborted = true;
+      it_abort = it;
+      left_after = next < ntiles;
+      break;
+    }
     float* st = stages + (it & 1) * sstride;
     float* Xs = st + (size_t)nb * BS;
     const int rb = 16 * warp;
@@ -349,14 +429,14 @@ __device__ __forceinline__ void tc_tfinalize(const int cta, const int ncta, int 
     if (row1 < n) *reinterpret_cast<float2*>(out + (size_t)8 * row1 + 2 * t) = make_float2(o[2], o[3]);
     __syncthreads();
   }
-  cp_async_wait_0();
+  tiles_end(tbar, aborted, it_abort, left_after, status);
 }
 
 // out[o] = Q[:, :J] Y[:, 8o : 8o + 8] for o < nout <= 4; the residual block copied to
 // out[resid_slot] when resid is given.  Ys: J x 8 nout (FP32) in shared memory.
 __device__ __forceinline__ void tc_trestart(const int cta, const int ncta, int n, const float* Q, size_t bstride,
                                             int nbk, int nout, const double* Y, float* out, size_t ostride,
-                                            const float* resid, int resid_slot) {
+                                            const float* resid, int resid_slot, int* status) {
   constexpr int TR = 128, BS = BlockStride<float>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* stages = reinterpret_cast<float*>(smem_raw);
@@ -367,14 +447,20 @@ __device__ __forceinline__ void tc_trestart(const int cta, const int ncta, int n
   for (int u = tid; u < J * ncol; u += blockDim.x) Ys[u] = (float)Y[(u / ncol) * JMAX + (u % ncol)];
   const int ntiles = (n + TR - 1) / TR;
   int tile = cta;
-  if (tile < ntiles) load_tile<float, TR>(stages, Q, bstride, nbk, nullptr, n, tile * TR);
-  cp_async_commit();
+  __shared__ uint64_t tbar[2];
+  tiles_begin(tbar);
+  bool aborted = false;
+  int it_abort = 0, left_after = 0;
+  if (tile < ntiles) tile_load<float, TR>(stages, Q, bstride, nbk, nullptr, n, tile * TR, &tbar[0]);
   for (int it = 0; tile < ntiles; ++it, tile += ncta) {
     const int next = tile + ncta;
-    if (next < ntiles) load_tile<float, TR>(stages + ((it + 1) & 1) * sstride, Q, bstride, nbk, nullptr, n, next * TR);
-    cp_async_commit();
-    cp_async_wait_1();
-    __syncthreads();
+    if (next < ntiles) tile_load<float, TR>(stages + ((it + 1) & 1) * sstride, Q, bstride, nbk, nullptr, n, next * TR, &tbar[(it + 1) & 1]);
+    if (!__syncthreads_and(tile_wait(&tbar[it & 1], (it >> 1) & 1, status))) {
+      aborted = true;
+      it_abort = it;
+      left_after = next < ntiles;
+      break;
+    }
     const float* st = stages + (it & 1) * sstride;
     const int rb = 16 * warp;
     float d[4][4];
@@ -409,7 +495,7 @@ __device__ __forceinline__ void tc_trestart(const int cta, const int ncta, int n
     }
     __syncthreads();
   }
-  cp_async_wait_0();
+  tiles_end(tbar, aborted, it_abort, left_after, status);
 }
 
 // ---- H = Q^T W --------------------------------------------------------------------------
@@ -449,10 +535,10 @@ __device__ __forceinline__ double sum_slots(const double* red, int nitems, int n
 template <typename T>
 __device__ __forceinline__ void k_tproj_dev(const int cta, const int ncta, int n, const T* USBS_RESTRICT Q, size_t bstride, int nb,
                                                const T* USBS_RESTRICT W, double* USBS_RESTRICT partials,
-                                               const int* USBS_RESTRICT mask) {
+                                               const int* USBS_RESTRICT mask, int* status) {
   if constexpr (sizeof(T) == 4) {
     if (mask && *mask == 0) return;
-    tc_tproj(cta, ncta, n, Q, bstride, nb, W, partials);
+    tc_tproj(cta, ncta, n, Q, bstride, nb, W, partials, status);
     return;
   }
   if (mask && *mask == 0) return;
@@ -470,14 +556,20 @@ __device__ __forceinline__ void k_tproj_dev(const int cta, const int ncta, int n
   for (int u = 0; u < 16; ++u) acc[u] = (T)0;
   const int ntiles = (n + TR - 1) / TR;
   int tile = cta;
-  if (tile < ntiles) load_tile<T, TR>(stages, Q, bstride, nb, W, n, tile * TR);
-  cp_async_commit();
+  __shared__ uint64_t tbar[2];
+  tiles_begin(tbar);
+  bool aborted = false;
+  int it_abort = 0, left_after = 0;
+  if (tile < ntiles) tile_load<T, TR>(stages, Q, bstride, nb, W, n, tile * TR, &tbar[0]);
   for (int it = 0; tile < ntiles; ++it, tile += ncta) {
     const int next = tile + ncta;
-    if (next < ntiles) load_tile<T, TR>(stages + ((it + 1) & 1) * sstride, Q, bstride, nb, W, n, next * TR);
-    cp_async_commit();
-    cp_async_wait_1();
-    __syncthreads();
+    if (next < ntiles) tile_load<T, TR>(stages + ((it + 1) & 1) * sstride, Q, bstride, nb, W, n, next * TR, &tbar[(it + 1) & 1]);
+    if (!__syncthreads_and(tile_wait(&tbar[it & 1], (it >> 1) & 1, status))) {
+      aborted = true;
+      it_abort = it;
+      left_after = next < ntiles;
+      break;
+    }
     const T* st = stages + (it & 1) * sstride;
     if (active) {
       const int b = item >> 2, a0 = 2 * (item & 3);
@@ -485,7 +577,7 @@ __device__ __forceinline__ void k_tproj_dev(const int cta, const int ncta, int n
     }
     __syncthreads();
   }
-  cp_async_wait_0();
+  tiles_end(tbar, aborted, it_abort, left_after, status);
   __syncthreads();
   double* red = reinterpret_cast<double*>(smem_raw);     // 8 warps x 32 slots x 16
   if (active) {
@@ -505,10 +597,10 @@ template <typename T>
 __device__ __forceinline__ void k_tupdate_dev(const int cta, const int ncta, int n, const T* USBS_RESTRICT Q, size_t bstride, int nb,
                                                  T* USBS_RESTRICT W, const double* USBS_RESTRICT Hred,
                                                  double* USBS_RESTRICT partials,
-                                                 const int* USBS_RESTRICT mask) {
+                                                 const int* USBS_RESTRICT mask, int* status) {
   if constexpr (sizeof(T) == 4) {
     if (mask && *mask == 0) return;
-    tc_tupdate(cta, ncta, n, Q, bstride, nb, W, Hred, partials);
+    tc_tupdate(cta, ncta, n, Q, bstride, nb, W, Hred, partials, status);
     return;
   }
   if (mask && *mask == 0) return;
@@ -531,15 +623,20 @@ __device__ __forceinline__ void k_tupdate_dev(const int cta, const int ncta, int
     for (int v = 0; v < 16; ++v) acc[u][v] = (T)0;
   const int ntiles = (n + TR - 1) / TR;
   int tile = cta;
-  if (tile < ntiles) load_tile<T, TR>(stages, Q, bstride, nb, W, n, tile * TR);
-  cp_async_commit();
-  // phase-1 mapping: row r = tid / 2 (2 passes when TR = 128 needs 2 rows per thread pair)
+  __shared__ uint64_t tbar[2];
+  tiles_begin(tbar);
+  bool aborted = false;
+  int it_abort = 0, left_after = 0;
+  if (tile < ntiles) tile_load<T, TR>(stages, Q, bstride, nb, W, n, tile * TR, &tbar[0]);
   for (int it = 0; tile < ntiles; ++it, tile += ncta) {
     const int next = tile + ncta;
-    if (next < ntiles) load_tile<T, TR>(stages + ((it + 1) & 1) * sstride, Q, bstride, nb, W, n, next * TR);
-    cp_async_commit();
-    cp_async_wait_1();
-    __syncthreads();
+    if (next < ntiles) tile_load<T, TR>(stages + ((it + 1) & 1) * sstride, Q, bstride, nb, W, n, next * TR, &tbar[(it + 1) & 1]);
+    if (!__syncthreads_and(tile_wait(&tbar[it & 1], (it >> 1) & 1, status))) {
+      aborted = true;
+      it_abort = it;
+      left_after = next < ntiles;
+      break;
+    }
     T* st = stages + (it & 1) * sstride;
     T* Xs = st + (size_t)nb * BlockStride<T>::value;                               // W tile, overwritten by X
     // phase 1: X = W - Q H, 4 columns per thread
@@ -579,7 +676,7 @@ __device__ __forceinline__ void k_tupdate_dev(const int cta, const int ncta, int
     }
     __syncthreads();
   }
-  cp_async_wait_0();
+  tiles_end(tbar, aborted, it_abort, left_after, status);
   __syncthreads();
   double* red = reinterpret_cast<double*>(smem_raw);     // 8 warps x nslot x 16
 #pragma unroll
@@ -605,10 +702,10 @@ template <typename T>
 __device__ __forceinline__ void k_tfinalize_dev(const int cta, const int ncta, int n, const T* USBS_RESTRICT Q, size_t bstride,
                                                    int nb, const T* W, const double* USBS_RESTRICT H2red,
                                                    const DevLanczos* USBS_RESTRICT lz, T* out,
-                                                   const int* USBS_RESTRICT mask, uint64_t seed) {
+                                                   const int* USBS_RESTRICT mask, uint64_t seed, int* status) {
   if constexpr (sizeof(T) == 4) {
     if (mask && *mask == 0) return;
-    tc_tfinalize(cta, ncta, n, Q, bstride, nb, W, H2red, lz, out, seed);
+    tc_tfinalize(cta, ncta, n, Q, bstride, nb, W, H2red, lz, out, seed, status);
     return;
   }
   if (mask && *mask == 0) return;
@@ -625,14 +722,20 @@ __device__ __forceinline__ void k_tfinalize_dev(const int cta, const int ncta, i
   if (tid < 8) dfc[tid] = lz->dcol[tid];
   const int ntiles = (n + TR - 1) / TR;
   int tile = cta;
-  if (tile < ntiles) load_tile<T, TR>(stages, Q, bstride, nb, W, n, tile * TR);
-  cp_async_commit();
+  __shared__ uint64_t tbar[2];
+  tiles_begin(tbar);
+  bool aborted = false;
+  int it_abort = 0, left_after = 0;
+  if (tile < ntiles) tile_load<T, TR>(stages, Q, bstride, nb, W, n, tile * TR, &tbar[0]);
   for (int it = 0; tile < ntiles; ++it, tile += ncta) {
     const int next = tile + ncta;
-    if (next < ntiles) load_tile<T, TR>(stages + ((it + 1) & 1) * sstride, Q, bstride, nb, W, n, next * TR);
-    cp_async_commit();
-    cp_async_wait_1();
-    __syncthreads();
+    if (next < ntiles) tile_load<T, TR>(stages + ((it + 1) & 1) * sstride, Q, bstride, nb, W, n, next * TR, &tbar[(it + 1) & 1]);
+    if (!__syncthreads_and(tile_wait(&tbar[it & 1], (it >> 1) & 1, status))) {
+      aborted = true;
+      it_abort = it;
+      left_after = next < ntiles;
+      break;
+    }
     T* st = stages + (it & 1) * sstride;
     T* Xs = st + (size_t)nb * BlockStride<T>::value;
     for (int p = tid; p < TR * 2; p += blockDim.x) {
@@ -673,7 +776,7 @@ __device__ __forceinline__ void k_tfinalize_dev(const int cta, const int ncta, i
     }
     __syncthreads();
   }
-  cp_async_wait_0();
+  tiles_end(tbar, aborted, it_abort, left_after, status);
 }
 
 
@@ -684,9 +787,9 @@ template <typename T>
 __device__ __forceinline__ void k_trestart_dev(const int cta, const int ncta, int n, const T* USBS_RESTRICT Q, size_t bstride, int nbk,
                                                   int nout, const double* USBS_RESTRICT Y,
                                                   T* USBS_RESTRICT out, size_t ostride,
-                                                  const T* USBS_RESTRICT resid, int resid_slot) {
+                                                  const T* USBS_RESTRICT resid, int resid_slot, int* status) {
   if constexpr (sizeof(T) == 4) {
-    tc_trestart(cta, ncta, n, Q, bstride, nbk, nout, Y, out, ostride, resid, resid_slot);
+    tc_trestart(cta, ncta, n, Q, bstride, nbk, nout, Y, out, ostride, resid, resid_slot, status);
     return;
   }
   constexpr int TR = TileRows<T>::value;
@@ -699,14 +802,20 @@ __device__ __forceinline__ void k_trestart_dev(const int cta, const int ncta, in
   for (int t = tid; t < J * ncol; t += blockDim.x) Ys[t] = (T)Y[(t / ncol) * JMAX + (t % ncol)];
   const int ntiles = (n + TR - 1) / TR;
   int tile = cta;
-  if (tile < ntiles) load_tile<T, TR>(stages, Q, bstride, nbk, nullptr, n, tile * TR);
-  cp_async_commit();
+  __shared__ uint64_t tbar[2];
+  tiles_begin(tbar);
+  bool aborted = false;
+  int it_abort = 0, left_after = 0;
+  if (tile < ntiles) tile_load<T, TR>(stages, Q, bstride, nbk, nullptr, n, tile * TR, &tbar[0]);
   for (int it = 0; tile < ntiles; ++it, tile += ncta) {
     const int next = tile + ncta;
-    if (next < ntiles) load_tile<T, TR>(stages + ((it + 1) & 1) * sstride, Q, bstride, nbk, nullptr, n, next * TR);
-    cp_async_commit();
-    cp_async_wait_1();
-    __syncthreads();
+    if (next < ntiles) tile_load<T, TR>(stages + ((it + 1) & 1) * sstride, Q, bstride, nbk, nullptr, n, next * TR, &tbar[(it + 1) & 1]);
+    if (!__syncthreads_and(tile_wait(&tbar[it & 1], (it >> 1) & 1, status))) {
+      aborted = true;
+      it_abort = it;
+      left_after = next < ntiles;
+      break;
+    }
     const T* st = stages + (it & 1) * sstride;
     // items (row pair, output block, column group): with nout < 4 the 8 columns of an
     // output block are split into 4 / nout groups so that every thread has work
@@ -754,7 +863,7 @@ __device__ __forceinline__ void k_trestart_dev(const int cta, const int ncta, in
     }
     __syncthreads();
   }
-  cp_async_wait_0();
+  tiles_end(tbar, aborted, it_abort, left_after, status);
 }
 
 }  // namespace

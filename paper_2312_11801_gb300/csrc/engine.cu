@@ -562,6 +562,10 @@ static int lanczos(Ctx* c, const double* y_dev, const void* start, void* out_vec
     USBS_CUDA_TRY(c, cudaMemcpyAsync(c->h_lz, c->lz, sizeof(DevLanczos), cudaMemcpyDeviceToHost,
                                      c->stream));
     USBS_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (c->h_lz->status == USBS_ETIMEOUT) {
+      c->err = "a staged tile copy did not complete within its wait limit";
+      return USBS_ETIMEOUT;
+    }
     if (c->h_lz->status != 0) {
       c->err = "non-finite Lanczos projection";
       return USBS_ENUMERIC;

@@ -23,32 +23,32 @@ namespace {
 template <typename T>
 __global__ void __launch_bounds__(256) k_tproj(int n, const T* __restrict__ Q, size_t bstride, int nb,
                                                const T* __restrict__ W, double* __restrict__ partials,
-                                               const int* __restrict__ mask) {
-  k_tproj_dev<T>(blockIdx.x, gridDim.x, n, Q, bstride, nb, W, partials, mask);
+                                               const int* __restrict__ mask, int* status) {
+  k_tproj_dev<T>(blockIdx.x, gridDim.x, n, Q, bstride, nb, W, partials, mask, status);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_tupdate(int n, const T* __restrict__ Q, size_t bstride, int nb,
                                                  T* __restrict__ W, const double* __restrict__ Hred,
                                                  double* __restrict__ partials,
-                                                 const int* __restrict__ mask) {
-  k_tupdate_dev<T>(blockIdx.x, gridDim.x, n, Q, bstride, nb, W, Hred, partials, mask);
+                                                 const int* __restrict__ mask, int* status) {
+  k_tupdate_dev<T>(blockIdx.x, gridDim.x, n, Q, bstride, nb, W, Hred, partials, mask, status);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_tfinalize(int n, const T* __restrict__ Q, size_t bstride,
                                                    int nb, const T* W, const double* __restrict__ H2red,
                                                    const DevLanczos* __restrict__ lz, T* out,
-                                                   const int* __restrict__ mask, uint64_t seed) {
-  k_tfinalize_dev<T>(blockIdx.x, gridDim.x, n, Q, bstride, nb, W, H2red, lz, out, mask, seed);
+                                                   const int* __restrict__ mask, uint64_t seed, int* status) {
+  k_tfinalize_dev<T>(blockIdx.x, gridDim.x, n, Q, bstride, nb, W, H2red, lz, out, mask, seed, status);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_trestart(int n, const T* __restrict__ Q, size_t bstride, int nbk,
                                                   int nout, const double* __restrict__ Y,
                                                   T* __restrict__ out, size_t ostride,
-                                                  const T* __restrict__ resid, int resid_slot) {
-  k_trestart_dev<T>(blockIdx.x, gridDim.x, n, Q, bstride, nbk, nout, Y, out, ostride, resid, resid_slot);
+                                                  const T* __restrict__ resid, int resid_slot, int* status) {
+  k_trestart_dev<T>(blockIdx.x, gridDim.x, n, Q, bstride, nbk, nout, Y, out, ostride, resid, resid_slot, status);
 }
 
 template <typename T>
@@ -109,11 +109,11 @@ template <typename T>
 int Orth<T>::proj(Ctx* c, const void* Qb, int nb, const void* W, const int* mask) {
   USBS_LAUNCH_B(c, USBS_KIND_REORTH, mask ? 0.0 : 8.0 * sizeof(T) * c->n * (nb + 1));
   set_attrs<T>();
-  // the epilogue reuses the stage buffers for 8 x 32 x 16 FP64 partial sums (= tc_red_bytes(4))
+  // the epilogue reuses the stage buffers for its warp partials
   const size_t sm = std::max(tile_smem<T>(nb, 0), sizeof(double) * 8 * 512);
   const int g = orth_grid(c, c->n, (const void*)k_tproj<T>, sm);
   k_tproj<T><<<g, 256, sm, c->stream>>>((int)c->n, (const T*)Qb, (size_t)c->n * 8, nb, (const T*)W,
-                                        c->partials, mask);
+                                        c->partials, mask, DEV_FIELD(c->lz, DevLanczos, status, int));
   return g;
 }
 
@@ -124,7 +124,7 @@ int Orth<T>::gram_xy(Ctx* c, const void* X, const void* Y) {
   const size_t sm = std::max(tile_smem<T>(1, 0), sizeof(double) * 8 * 512);
   const int g = orth_grid(c, c->n, (const void*)k_tproj<T>, sm);
   k_tproj<T><<<g, 256, sm, c->stream>>>((int)c->n, (const T*)X, (size_t)c->n * 8, 1, (const T*)Y,
-                                        c->partials, nullptr);
+                                        c->partials, nullptr, DEV_FIELD(c->lz, DevLanczos, status, int));
   return g;
 }
 
@@ -132,14 +132,14 @@ template <typename T>
 int Orth<T>::update(Ctx* c, const void* Qb, int nb, void* W, const int* mask) {
   USBS_LAUNCH_B(c, USBS_KIND_REORTH_UPDATE, mask ? 0.0 : 8.0 * sizeof(T) * c->n * (nb + 2));
   set_attrs<T>();
-  // the epilogue reuses the stage buffers for its FP64 warp partials: FP32 (tensor cores)
-  // 8 warps x 5 pairs x 32 x 4; FP64 8 warps x (32 or 64) slots x 16
+  // the epilogue reuses the stage buffers for its warp partials: FP32 (tensor cores)
+  // 8 warps x 5 pairs x 32 x 4 floats; FP64 8 warps x (32 or 64) slots x 16 doubles
   const size_t red = sizeof(T) == 4 ? tc_red_bytes(5)
                                     : sizeof(double) * 8 * (4 * (nb + 1) <= 32 ? 32 : 64) * 16;
   const size_t sm = std::max(tile_smem<T>(nb, 8 * 64), red);
   const int g = orth_grid(c, c->n, (const void*)k_tupdate<T>, sm);
   k_tupdate<T><<<g, 256, sm, c->stream>>>((int)c->n, (const T*)Qb, (size_t)c->n * 8, nb, (T*)W,
-                                          c->red + RED_H, c->partials, mask);
+                                          c->red + RED_H, c->partials, mask, DEV_FIELD(c->lz, DevLanczos, status, int));
   return g;
 }
 
@@ -151,7 +151,7 @@ void Orth<T>::finalize(Ctx* c, const void* Qb, int nb, const void* W, void* out,
   const size_t sm = tile_smem<T>(nb, 8 * 64 + 64);
   k_tfinalize<T><<<orth_grid(c, c->n, (const void*)k_tfinalize<T>, sm), 256, sm, c->stream>>>(
       (int)c->n, (const T*)Qb, (size_t)c->n * 8, nb, (const T*)W, c->red + RED_H2, c->lz, (T*)out,
-      mask, seed);
+      mask, seed, DEV_FIELD(c->lz, DevLanczos, status, int));
 }
 
 template <typename T>
@@ -162,7 +162,7 @@ void Orth<T>::restart(Ctx* c, const void* Qb, int J, int nout, const double* Y, 
   const size_t sm = sizeof(T) * (2 * (size_t)(J / 8) * BlockStride<T>::value + (size_t)J * nout * 8);
   k_trestart<T><<<orth_grid(c, c->n, (const void*)k_trestart<T>, sm), 256, sm, c->stream>>>(
       (int)c->n, (const T*)Qb, (size_t)c->n * 8, J / 8, nout, Y, (T*)out, (size_t)c->n * 8,
-      (const T*)resid, resid_slot);
+      (const T*)resid, resid_slot, DEV_FIELD(c->lz, DevLanczos, status, int));
 }
 
 template struct Orth<float>;
