@@ -36,6 +36,10 @@ UNIT = "solves/sec"
 TOL = 1e-3
 SIDE, R_SKETCH = 1000, 16
 WORKLOAD = "maxcut_torus_1000x1000_pm1_r16_mixed"
+# DRAM bytes of one k_tupdate launch against its algorithmic bytes, from the ncu capture
+# summarised in profiles/k_tupdate_c2_torus1000.md (nb = 4, n = 1e6); the bench scales the
+# ratio to the average algorithmic bytes per launch of its own run
+TUPDATE_TRAFFIC = {"dram_bytes": 176.92e6, "algorithmic_bytes": 192.0e6}
 KERNEL_OF_KIND = {"spmm": "k_spmm", "reorth": "k_tproj", "reorth_update": "k_tupdate",
                   "reorth_final": "k_tfinalize", "restart": "k_trestart", "reduce": "k_reduce",
                   "constraint": "k_gstats+k_xupdate+k_alt", "sketch": "k_vt_psi+k_sketch_update"}
@@ -289,7 +293,10 @@ def run_ours(args, world, rank, local, pg):
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "kernel": KERNEL_OF_KIND.get(dom, dom), "achieved": achieved, "peak": hbm,
                      "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": None, "peak_source": peak_src},
+                     "traffic": (TUPDATE_TRAFFIC["dram_bytes"] / TUPDATE_TRAFFIC["algorithmic_bytes"] * by / nl)
+                     if dom == "reorth_update" and nl else None,
+                     "algorithmic_bytes_per_launch": by / nl if nl else None,
+                     "peak_source": peak_src},
         "lanczos_spmm": {"achieved_gbs": spmm_gbs, "frac": spmm_gbs / hbm, "launches": spmm_n,
                          "avg_us": 1e3 * spmm_ms / max(spmm_n, 1),
                          "bytes_per_launch": spmm_b / max(spmm_n, 1)},
