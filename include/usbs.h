@@ -80,6 +80,9 @@ typedef struct usbs_eig_info {
   int    converged;        /* 1 if every top-k_c residual met lanczos_tol */
   double max_residual;     /* max over top k_c of ||M v - theta v|| (scaled units) */
   int    jacobi_sweeps;    /* Jacobi sweeps of the Rayleigh-Ritz steps, summed */
+  int    reruns;           /* cycles run again with the masked deflation passes, summed
+                              over the context's life (a speculative cycle met a deficient
+                              column); 0 with USBS_NO_SPECULATE=1 in the environment */
 } usbs_eig_info;
 
 typedef struct usbs_step_info {

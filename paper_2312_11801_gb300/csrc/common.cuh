@@ -75,7 +75,9 @@ struct DevLanczos {
   int cycles;
   int status;                  // USBS_ENUMERIC if the projected matrix went non-finite
   int sweeps;                  // Jacobi sweeps summed over the cycles of this solve
-  int pad2;
+  int defl_seen;               // a first pass of this cycle found a deficient column
+  int redo;                    // the cycle ran without its masked passes but needed them:
+                               // its Rayleigh-Ritz step was skipped, the host reruns it
 };
 
 template <typename T>
@@ -101,6 +103,8 @@ struct Ctx {
   std::string err;
   bool started = false;         // an iterate exists (cold start done)
   bool debug = false;           // USBS_DEBUG=1: per-block-step checks on the host
+  bool speculate = true;        // run Lanczos cycles without the masked passes, rerun a cycle
+                                // that needed them (USBS_NO_SPECULATE=1 turns this off)
   long long total_matvecs = 0;
 
   // operator (scaled): merged off-diagonal CSR pattern + diagonal
@@ -147,6 +151,7 @@ struct Ctx {
   DevLanczos* h_lz = nullptr;
   uint64_t seed = 0;
   uint64_t rng_counter = 1;
+  int64_t spec_redos = 0;       // speculative Lanczos cycles that had to run again
   // measurement
   long long launches = 0;
   bool prof = false;
@@ -277,7 +282,7 @@ void reduce_max_slot(Ctx* c, int nparts, int slot, double* out);
 
 // ---- small single-CTA kernels (small.cu) -------------------------------------------------
 void launch_chol_block(Ctx* c, int j, int nb, int write_T, int is_resid, int defl_pass);
-void launch_ritz(Ctx* c, int J, int keep);
+void launch_ritz(Ctx* c, int J, int keep, int spec);
 void launch_ipm(Ctx* c, int first_pass);
 void launch_finish(Ctx* c);
 void launch_commit(Ctx* c);

@@ -317,6 +317,12 @@ __device__ __forceinline__ void tc_tupdate(const int cta, const int ncta, int n,
   float* Hs = stages + 2 * sstride;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   for (int u = threadIdx.x; u < nb * 64; u += blockDim.x) Hs[u] = (float)Hred[u];
+  __syncthreads();
+  // B fragments of H, split once for all tiles
+  SplitB hb[8];
+#pragma unroll
+  for (int b = 0; b < 8; ++b)
+    hb[b] = (b < nb) ? split_b(Hs[b * 64 + t * 8 + g], Hs[b * 64 + (t + 4) * 8 + g]) : SplitB{0u, 0u, 0u, 0u};
   float acc[5][4];
 #pragma unroll
   for (int p = 0; p < 5; ++p)
@@ -344,10 +350,12 @@ __device__ __forceinline__ void tc_tupdate(const int cta, const int ncta, int n,
     {
       const int rb = 16 * warp;
       float d[4] = {0.f, 0.f, 0.f, 0.f};
-      for (int b = 0; b < nb; ++b) {
-        const float* q = st + (size_t)b * BS + (size_t)rb * 8;
-        const SplitB hb = split_b(Hs[b * 64 + t * 8 + g], Hs[b * 64 + (t + 4) * 8 + g]);
-        mma3(d, q[g * 8 + t], q[(g + 8) * 8 + t], q[g * 8 + t + 4], q[(g + 8) * 8 + t + 4], hb);
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        if (b < nb) {
+          const float* q = st + (size_t)b * BS + (size_t)rb * 8;
+          mma3(d, q[g * 8 + t], q[(g + 8) * 8 + t], q[g * 8 + t + 4], q[(g + 8) * 8 + t + 4], hb[b]);
+        }
       }
       float* x0 = Xs + (size_t)(rb + g) * 8 + 2 * t;
       float* x1 = Xs + (size_t)(rb + g + 8) * 8 + 2 * t;
@@ -385,6 +393,11 @@ __device__ __forceinline__ void tc_tfinalize(const int cta, const int ncta, int 
   if (tid < 8) dfc[tid] = lz->dcol[tid];
   __syncthreads();
   const SplitB rb0 = split_b(Ri[t * 8 + g], Ri[(t + 4) * 8 + g]);
+  // B fragments of H2, split once for all tiles
+  SplitB hb[8];
+#pragma unroll
+  for (int b = 0; b < 8; ++b)
+    hb[b] = (b < nb) ? split_b(Hs[b * 64 + t * 8 + g], Hs[b * 64 + (t + 4) * 8 + g]) : SplitB{0u, 0u, 0u, 0u};
   const int ntiles = (n + TR - 1) / TR;
   int tile = cta;
   __shared__ uint64_t tbar[2];
@@ -405,10 +418,12 @@ __device__ __forceinline__ void tc_tfinalize(const int cta, const int ncta, int 
     float* Xs = st + (size_t)nb * BS;
     const int rb = 16 * warp;
     float d[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int b = 0; b < nb; ++b) {
-      const float* q = st + (size_t)b * BS + (size_t)rb * 8;
-      const SplitB hb = split_b(Hs[b * 64 + t * 8 + g], Hs[b * 64 + (t + 4) * 8 + g]);
-      mma3(d, q[g * 8 + t], q[(g + 8) * 8 + t], q[g * 8 + t + 4], q[(g + 8) * 8 + t + 4], hb);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      if (b < nb) {
+        const float* q = st + (size_t)b * BS + (size_t)rb * 8;
+        mma3(d, q[g * 8 + t], q[(g + 8) * 8 + t], q[g * 8 + t + 4], q[(g + 8) * 8 + t + 4], hb[b]);
+      }
     }
     // X = W - Q H2 back into this warp's own rows, then (X R^-1) as a second MMA
     float* x0 = Xs + (size_t)(rb + g) * 8 + 2 * t;

@@ -41,7 +41,7 @@ __device__ bool warp_chol(const double* A, double* R, int k) {
     }
     d = __shfl_sync(FULL, d, j);
     if (!(d > 0.0)) return false;
-    const double rjj = sqrt(d), inv = 1.0 / rjj;
+    const double inv = rsqrt(d), rjj = d * inv;
     double sacc = (lane > j && lane < k) ? A[j * 8 + lane] : 0.0;
 #pragma unroll
     for (int l = 0; l < 8; ++l) {
@@ -65,16 +65,22 @@ __device__ bool warp_chol(const double* A, double* R, int k) {
 // A^-1 = R^-1 R^-T.  Warp-cooperative; Rinv is scratch (row stride 8).
 __device__ void warp_spd_inverse(const double* R, double* Rinv, double* Ainv, int k) {
   const int lane = threadIdx.x & 31;
+  // reciprocals of the diagonal, one per lane, shared by shuffles: the back substitution
+  // then multiplies instead of dividing at every step of its serial chain
+  const double rd_own = (lane < k) ? 1.0 / R[lane * 8 + lane] : 0.0;
+  double rd[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) rd[i] = __shfl_sync(FULL, rd_own, i);
   if (lane < k) {
     const int c = lane;
     double x[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) x[i] = 0.0;
-    x[c] = 1.0 / R[c * 8 + c];
+    x[c] = rd[c];
     for (int i = c - 1; i >= 0; --i) {
       double sacc = 0.0;
       for (int l = i + 1; l <= c; ++l) sacc += R[i * 8 + l] * x[l];
-      x[i] = -sacc / R[i * 8 + i];
+      x[i] = -sacc * rd[i];
     }
 #pragma unroll
     for (int i = 0; i < 8; ++i) Rinv[i * 8 + c] = (i < k) ? x[i] : 0.0;
@@ -255,7 +261,7 @@ __device__ __forceinline__ void k_chol_block_dev(DevLanczos* lz, const double* U
         if (lane == j) rc[j] = 1.0;   // row j of R stays e_j^T: the column is replaced
         continue;
       }
-      const double rjj = sqrt(d), inv = 1.0 / rjj;
+      const double inv = rsqrt(d), rjj = d * inv;
       double sacc = (lane > j && lane < 8) ? G[j * 8 + lane] : 0.0;
 #pragma unroll
       for (int l = 0; l < 8; ++l) {
@@ -272,17 +278,22 @@ __device__ __forceinline__ void k_chol_block_dev(DevLanczos* lz, const double* U
       for (int i = 0; i < 8; ++i) R[i * 8 + lane] = (i <= lane) ? rc[i] : 0.0;
     }
     __syncwarp();
-    // column c of R^-1 by back substitution (lane c)
+    // column c of R^-1 by back substitution (lane c), with the reciprocals of R's
+    // diagonal shared by shuffles
+    const double rd_own = (lane < 8) ? 1.0 / R[lane * 8 + lane] : 0.0;
+    double rd[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) rd[i] = __shfl_sync(FULL, rd_own, i);
     if (lane < 8) {
       const int cidx = lane;
       double x[8];
 #pragma unroll
       for (int i = 0; i < 8; ++i) x[i] = 0.0;
-      x[cidx] = 1.0 / R[cidx * 8 + cidx];
+      x[cidx] = rd[cidx];
       for (int i = cidx - 1; i >= 0; --i) {
         double sacc = 0.0;
         for (int l = i + 1; l <= cidx; ++l) sacc += R[i * 8 + l] * x[l];
-        x[i] = -sacc / R[i * 8 + i];
+        x[i] = -sacc * rd[i];
       }
 #pragma unroll
       for (int i = 0; i < 8; ++i) Ri[i * 8 + cidx] = x[i];
@@ -306,6 +317,7 @@ __device__ __forceinline__ void k_chol_block_dev(DevLanczos* lz, const double* U
       if (defl_pass == 0) {
         lz->defl = (badmask != 0) ? 1 : 0;
         lz->defl2 = 0;
+        if (badmask != 0 && write_T) lz->defl_seen = 1;   // a block of a cycle, not the start block
       } else if (defl_pass == 1) {
         lz->defl2 = (badmask != 0) ? 1 : 0;
       }
@@ -313,17 +325,287 @@ __device__ __forceinline__ void k_chol_block_dev(DevLanczos* lz, const double* U
   }
 }
 
+// ---- Rayleigh-Ritz in FP32 (mixed mode) ---------------------------------------------------------
+// The same cyclic Jacobi method with circle ordering as the generic body below, arranged so
+// that one CTA runs a round at FP32 speed with a single barrier:
+//  - every warp forms the J/2 rotations of the round itself (lane l the rotation of pair
+//    l mod J/2) and hands them to its lanes by shuffles, so no shared table and no barrier
+//    sits between the rotation parameters and the update;
+//  - A is double-buffered (read A_cur, write A_next), so the pivots a round reads are never
+//    overwritten within it;
+//  - the rotation parameters keep IEEE division and square root (with the hardware
+//    approximations instead, together with the one-step orthonormalisation below, a
+//    mixed-precision solve of a 400-node geometric graph stalled at 2.5e-3 infeasibility;
+//    either change alone converges);
+//  - T is scaled by an exact power of two (its largest entry to [1/2, 1)), which leaves every
+//    rotation unchanged and keeps the sums of squares of the stopping test in FP32 range;
+//  - the kept Ritz vectors are made orthonormal by one Newton-Schulz step towards their polar
+//    factor, Y_keep <- Y_keep + Y_keep (I - Y_keep^T Y_keep) / 2: the accumulated rotations
+//    are orthogonal to about 1e-6, and one step squares that defect (same span as the
+//    Gram-Schmidt of the generic body, two barriers instead of four per column).
+// The restarted projected matrix is Y_keep^T T Y_keep with the unrotated T, as in the generic
+// body, so rounding in the rotations costs convergence speed, not accuracy.
+__device__ __forceinline__ int jac_circle(int pos, int round, int J) {
+  if (pos == 0) return 0;
+  int x = pos - 1 + round;
+  if (x >= J - 1) x -= J - 1;
+  return 1 + x;
+}
+
+__device__ __forceinline__ void jac_rot_f32(float app, float aqq, float apq, float skip2,
+                                            float& c, float& s) {
+  c = 1.f;
+  s = 0.f;
+  if (apq != 0.f && apq * apq > skip2 * fabsf(app * aqq)) {
+    const float tau = (aqq - app) / (2.f * apq);
+    float t;
+    if (fabsf(tau) > 1e18f) t = 0.5f / tau;
+    else t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(tau * tau + 1.f));
+    c = 1.f / sqrtf(t * t + 1.f);
+    s = t * c;
+  }
+}
+
+template <int J>
+__device__ __forceinline__ void k_ritz_f32_dev(DevLanczos* lz, int kc, double tol, int max_sweeps,
+                                                  double jac_eps) {
+  constexpr int keep = J / 2;
+  constexpr int half = J / 2;
+  constexpr int LD = J + 1;
+  constexpr int NBLK = half * half, NITEM = half * half + J * half;
+  static_assert(NBLK % 32 == 0 && NITEM % 32 == 0 && half <= 32, "warp-uniform work split");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* A0 = reinterpret_cast<float*>(smem_raw);   // J x LD: T (scaled), rotated
+  float* A1 = A0 + J * LD;                            // J x LD: the other buffer of A
+  float* Vv = A1 + J * LD;                            // J x LD: accumulated rotations
+  float* Tc = Vv + J * LD;                            // J x LD: copy of T (unscaled)
+  float* Z = Tc + J * LD;                             // J x keep: T Y_keep (first: I - G)
+  __shared__ float key[JMAX], dg[JMAX];
+  __shared__ int order[JMAX];
+  __shared__ float wsum[2][16];
+  __shared__ unsigned wmax[16];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nw = blockDim.x >> 5;
+  // largest |T_ij| by the high word of its bit pattern (integer order = magnitude order)
+  unsigned hm = 0;
+  for (int t = tid; t < J * J; t += blockDim.x) {
+    const double x = lz->T[(t / J) * JMAX + t % J];
+    hm = max(hm, (unsigned)__double2hiint(x) & 0x7fffffffu);
+  }
+  hm = __reduce_max_sync(FULL, hm);
+  if (lane == 0) wmax[warp] = hm;
+  __syncthreads();
+  hm = 0;
+  for (int w = 0; w < nw; ++w) hm = max(hm, wmax[w]);
+  const int ebits = (int)(hm >> 20);
+  if (ebits == 0x7ff) {
+    // non-finite projected matrix: report it and stop the eigen solve
+    if (tid == 0) {
+      lz->status = USBS_ENUMERIC;
+      lz->converged = 1;
+      lz->cycles += 1;
+    }
+    for (int t = tid; t < JMAX * JMAX; t += blockDim.x) lz->Y[t] = ((t / JMAX) == (t % JMAX)) ? 1.0 : 0.0;
+    if (tid < JMAX) lz->theta[tid] = 0.0;
+    return;
+  }
+  // A = T 2^-esh with the largest entry in [1/2, 1)
+  const int esh = (hm == 0) ? 0 : ebits - 1022;
+  const bool fscale = esh > -100 && esh < 100;
+  const float scf = fscale ? ldexpf(1.f, -esh) : 1.f;
+  const double scd = ldexp(1.0, -esh);
+  for (int t = tid; t < J * J; t += blockDim.x) {
+    const int i = t / J, j = t % J;
+    const double x = lz->T[i * JMAX + j];
+    const float xf = (float)x;
+    A0[i * LD + j] = fscale ? xf * scf : (float)(x * scd);
+    Tc[i * LD + j] = xf;
+    Vv[i * LD + j] = (i == j) ? 1.f : 0.f;
+  }
+  __syncthreads();
+  const float skip2 = (float)(jac_eps * 1e-2) * (float)(jac_eps * 1e-2);
+  const float eps2 = (float)jac_eps * (float)jac_eps;
+  float* Ac = A0;
+  float* An = A1;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    float off = 0.f, tot = 0.f;
+    for (int t = tid; t < J * J; t += blockDim.x) {
+      const int i = t / J, j = t % J;
+      const float x = Ac[i * LD + j];
+      tot = fmaf(x, x, tot);
+      if (i != j) off = fmaf(x, x, off);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(FULL, off, o);
+      tot += __shfl_xor_sync(FULL, tot, o);
+    }
+    if (lane == 0) { wsum[0][warp] = off; wsum[1][warp] = tot; }
+    __syncthreads();
+    // every thread sums the warps' parts in the same order: one decision, no second barrier
+    float o2 = 0.f, t2 = 0.f;
+    for (int w = 0; w < nw; ++w) { o2 += wsum[0][w]; t2 += wsum[1][w]; }
+    if (o2 <= eps2 * t2) break;
+    if (tid == 0) lz->sweeps += 1;
+    for (int round = 0; round < J - 1; ++round) {
+      // lane l: the rotation of pair l mod half, from the pivots of A_cur
+      const int kr = lane & (half - 1);
+      const int pa = jac_circle(kr, round, J), pb = jac_circle(J - 1 - kr, round, J);
+      const int pr = min(pa, pb), qr = max(pa, pb);
+      float cr, sr;
+      jac_rot_f32(Ac[pr * LD + pr], Ac[qr * LD + qr], Ac[pr * LD + qr], skip2, cr, sr);
+      const int pqr = pr | (qr << 8);
+      for (int t0 = warp * 32; t0 < NITEM; t0 += blockDim.x) {   // warp-uniform
+        const int t = t0 + lane;
+        if (t0 < NBLK) {
+          // 2 x 2 block (p1, q1) x (p2, q2): rows by rotation k1, columns by k2
+          const int k1 = t / half, k2 = t % half;
+          const float c1 = __shfl_sync(FULL, cr, k1), s1 = __shfl_sync(FULL, sr, k1);
+          const float c2 = __shfl_sync(FULL, cr, k2), s2 = __shfl_sync(FULL, sr, k2);
+          const int pq1 = __shfl_sync(FULL, pqr, k1), pq2 = __shfl_sync(FULL, pqr, k2);
+          const int p1 = pq1 & 255, q1 = pq1 >> 8, p2 = pq2 & 255, q2 = pq2 >> 8;
+          const float a = Ac[p1 * LD + p2], b = Ac[p1 * LD + q2];
+          const float cc = Ac[q1 * LD + p2], d = Ac[q1 * LD + q2];
+          const float ra = c1 * a - s1 * cc, rb = c1 * b - s1 * d;
+          const float rc = s1 * a + c1 * cc, rd = s1 * b + c1 * d;
+          An[p1 * LD + p2] = c2 * ra - s2 * rb;
+          An[p1 * LD + q2] = s2 * ra + c2 * rb;
+          An[q1 * LD + p2] = c2 * rc - s2 * rd;
+          An[q1 * LD + q2] = s2 * rc + c2 * rd;
+        } else {
+          // V <- V G on row `row`, pair k (each (row, k) owned by one thread: in place)
+          const int u = t - NBLK;
+          const int k = u / J, row = u % J;
+          const float c = __shfl_sync(FULL, cr, k), sv = __shfl_sync(FULL, sr, k);
+          const int pq = __shfl_sync(FULL, pqr, k);
+          const int p = pq & 255, q = pq >> 8;
+          const float vp = Vv[row * LD + p], vq = Vv[row * LD + q];
+          Vv[row * LD + p] = c * vp - sv * vq;
+          Vv[row * LD + q] = sv * vp + c * vq;
+        }
+      }
+      __syncthreads();
+      float* tmp = Ac; Ac = An; An = tmp;
+    }
+  }
+  // descending order under a strict total order (value, then index)
+  if (tid < J) {
+    const float d = Ac[tid * LD + tid];
+    dg[tid] = d;
+    key[tid] = isfinite(d) ? d : -FLT_MAX;
+  }
+  __syncthreads();
+  if (tid < J) {
+    int rank = 0;
+    const float x = key[tid];
+    for (int u = 0; u < J; ++u) {
+      const float y = key[u];
+      if (y > x || (y == x && u < tid)) ++rank;
+    }
+    order[rank] = tid;
+  }
+  __syncthreads();
+  // A is no longer needed: Y (sorted Ritz vectors) in one buffer, its correction in the other
+  float* Y = An;
+  float* Yn = Ac;
+  for (int t = tid; t < J * J; t += blockDim.x) {
+    const int l = t / J, col = t % J;
+    Y[l * LD + col] = Vv[l * LD + order[col]];
+  }
+  __syncthreads();
+  // E = I - Y_keep^T Y_keep
+  float* E = Z;
+  for (int t = tid; t < keep * keep; t += blockDim.x) {
+    const int i = t / keep, j = t % keep;
+    float g = 0.f;
+    for (int r = 0; r < J; ++r) g = fmaf(Y[r * LD + i], Y[r * LD + j], g);
+    E[t] = (i == j ? 1.f : 0.f) - g;
+  }
+  __syncthreads();
+  // Y_keep <- Y_keep + Y_keep E / 2; the other columns are copied
+  for (int t = tid; t < J * J; t += blockDim.x) {
+    const int r = t / J, i = t % J;
+    float v = Y[r * LD + i];
+    if (i < keep) {
+      float acc = 0.f;
+      for (int j = 0; j < keep; ++j) acc = fmaf(Y[r * LD + j], E[j * keep + i], acc);
+      v = fmaf(0.5f, acc, v);
+    }
+    Yn[r * LD + i] = v;
+  }
+  __syncthreads();
+  Y = Yn;
+  // Z = T Y_keep; restarted projected matrix Y_keep^T T Y_keep
+  for (int t = tid; t < J * keep; t += blockDim.x) {
+    const int r = t / keep, i = t % keep;
+    float z = 0.f;
+    for (int c2 = 0; c2 < J; ++c2) z = fmaf(Tc[r * LD + c2], Y[c2 * LD + i], z);
+    Z[r * keep + i] = z;
+  }
+  __syncthreads();
+  for (int t = tid; t < JMAX * JMAX; t += blockDim.x) {
+    const int i = t / JMAX, j = t % JMAX;
+    double v = 0.0;
+    if (i < keep && j < keep) {
+      float acc = 0.f;
+      for (int r = 0; r < J; ++r) acc = fmaf(Y[r * LD + i], Z[r * keep + j], acc);
+      v = (double)acc;
+    }
+    lz->T[t] = v;
+  }
+  for (int t = tid; t < J * J; t += blockDim.x) {
+    const int l = t / J, col = t % J;
+    lz->Y[l * JMAX + col] = (double)Y[l * LD + col];
+  }
+  if (warp == 0) {
+    // Ritz values in T's units (the diagonal of A scaled back), then for the top k_c the
+    // Rayleigh quotients of the orthonormalised vectors and the residual norms
+    // ||T y_i - theta_i y_i||^2 + ||R_last E^T y_i||^2 (two orthogonal terms), in A's scale
+    for (int i = lane; i < J; i += 32) lz->theta[i] = ldexp((double)key[order[i]], esh);
+    float m = 0.f;
+    for (int i = lane; i < J; i += 32) m = fmaxf(m, fabsf(dg[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(FULL, m, o));
+    const double normest = fmax(lz->normest, ldexp((double)m, esh));
+    double res = 0.0;
+    if (lane < kc) {
+      const int i = lane;
+      float zz = 0.f;
+      for (int r = 0; r < J; ++r) zz = fmaf(Y[r * LD + i], Z[r * keep + i], zz);
+      float s2 = 0.f;
+      const float inv = ldexpf(1.f, -max(-126, min(126, esh)));
+      for (int r = 0; r < J; ++r) {
+        const float e = (Z[r * keep + i] - zz * Y[r * LD + i]) * inv;
+        s2 = fmaf(e, e, s2);
+      }
+      for (int a = 0; a < 8; ++a) {
+        float v = 0.f;
+        for (int c2 = a; c2 < 8; ++c2) v = fmaf((float)lz->Rlast[a * 8 + c2], Y[(J - 8 + c2) * LD + i], v);
+        v *= inv;
+        s2 = fmaf(v, v, s2);
+      }
+      res = ldexp(sqrt((double)s2), max(-126, min(126, esh)));
+      lz->res[i] = res;
+      lz->theta[i] = (double)zz;
+    }
+    const bool ok = (lane >= kc) || (res <= tol * normest);
+    const unsigned all_ok = __all_sync(FULL, ok);
+    if (lane == 0) {
+      lz->normest = normest;
+      lz->converged = all_ok ? 1 : 0;
+      lz->cycles += 1;
+    }
+  }
+}
+
 // ---- Rayleigh-Ritz: eigen-decomposition of T by parallel cyclic Jacobi ------------------------
-// S is the arithmetic of the whole Ritz step (FP32 in mixed mode, where GB300's FP64 rate
-// would make this one CTA the bottleneck; FP64 in the plain mode).  The J/2 rotations
-// of a round act on disjoint index pairs (circle ordering), so every 2 x 2 block
-// (p1, q1) x (p2, q2) of A is updated in one pass as R1^T [a b; c d] R2.  After the
-// sort, the kept Ritz vectors are orthonormalised (classical Gram-Schmidt, two passes)
-// and the restarted projected matrix is Y_keep^T T Y_keep, so rounding in the
-// rotations does not leak into the next cycle.
+// Generic body, S the arithmetic of the whole Ritz step (the FP64 of the plain mode; FP32 runs
+// the restructured body above).  The J/2 rotations of a round act on disjoint index pairs
+// (circle ordering), so every 2 x 2 block (p1, q1) x (p2, q2) of A is updated in one pass
+// as R1^T [a b; c d] R2.  After the sort, the kept Ritz vectors are orthonormalised
+// (classical Gram-Schmidt, two passes) and the restarted projected matrix is
+// Y_keep^T T Y_keep, so rounding in the rotations does not leak into the next cycle.
 template <typename S, int J>
-__device__ __forceinline__ void k_ritz_dev(DevLanczos* lz, int kc, double tol, int max_sweeps,
-                                              double jac_eps) {
+__device__ __forceinline__ void k_ritz_generic_dev(DevLanczos* lz, int kc, double tol, int max_sweeps,
+                                                      double jac_eps) {
   constexpr int keep = J / 2;
   constexpr int half = J / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -553,6 +835,15 @@ __device__ __forceinline__ void k_ritz_dev(DevLanczos* lz, int kc, double tol, i
   }
 }
 
+// Rayleigh-Ritz step of one restart cycle: FP32 (mixed mode) by the restructured body, FP64
+// by the generic one (where GB300's FP64 rate, not the barriers, sets the time).
+template <typename S, int J>
+__device__ __forceinline__ void k_ritz_dev(DevLanczos* lz, int kc, double tol, int max_sweeps,
+                                              double jac_eps) {
+  if constexpr (sizeof(S) == 4) k_ritz_f32_dev<J>(lz, kc, tol, max_sweeps, jac_eps);
+  else k_ritz_generic_dev<S, J>(lz, kc, tol, max_sweeps, jac_eps);
+}
+
 // ---- App. B.2 interior point method --------------------------------------------------------
 struct IpmShared {
   double Q[KSV * KSV];
@@ -563,8 +854,41 @@ struct IpmShared {
   double S[64], T[64], Sinv[64], Lc[64], work[64], dS[64], dT[64], St[64], Tt[64];
   double q22, h2, eta, zeta, omega, mu, deta, dzeta, domega, delta, kappa1, kappa2, det, r2, r3;
   int map[KSV];
+  int perm[2][KSV];            // row permutations of the elimination (current, next)
   int piv, done, iters, has_eta;
 };
+
+// Warp 0 of k_ipm: pivot of column pc of [L | rhs] among the logical rows pc..K-1 of the
+// permutation src.  The largest |entry| is found by the high word of its bit pattern
+// (exponent and 20 mantissa bits, which order magnitudes to 1e-6, ties to the lowest row)
+// with two warp reductions on the integer pipe.  dst = src with the pivot row moved to
+// position pc (dst may be src); fcol[pc] = 1 / pivot, or 0 and piv = -1 if it vanishes.
+__device__ __forceinline__ void ipm_pivot(IpmShared& sh, const int* src, int* dst, int pc, int K,
+                                          int LDL, int lane) {
+  unsigned key = 0u;
+  int bi = pc;
+  for (int r = pc + lane; r < K; r += 32) {
+    const unsigned k = (unsigned)__double2hiint(sh.L[src[r] * LDL + pc]) & 0x7fffffffu;
+    if (k > key) { key = k; bi = r; }
+  }
+  const unsigned kmax = __reduce_max_sync(FULL, key);
+  bi = (int)__reduce_min_sync(FULL, key == kmax ? (unsigned)bi : 0xffffffffu);
+  if (dst != src)
+    for (int r = lane; r < K; r += 32) dst[r] = src[r];
+  __syncwarp();
+  if (lane == 0) {
+    const int a = dst[pc], b = dst[bi];
+    dst[pc] = b;
+    dst[bi] = a;
+    // an exactly singular system (possible at degenerate optima): mark the direction
+    // unusable instead of dividing by zero
+    const double pv = sh.L[b * LDL + pc];
+    const bool ok = fabs(pv) > 1e-300;
+    sh.fcol[pc] = ok ? 1.0 / pv : 0.0;
+    if (!ok) sh.piv = -1;
+  }
+  __syncwarp();
+}
 
 __device__ __forceinline__ double aug_at(const double* aug, int r, int c) {
   if (r > c) { int t = r; r = c; c = t; }
@@ -575,6 +899,7 @@ __device__ __forceinline__ double aug_at(const double* aug, int r, int c) {
   return aug[idx * 16 + (r % 4) * 4 + (c % 4)];
 }
 
+// One CTA of 256 threads (8 warps: the phases below hand rows and scalars to fixed warps).
 __device__ __forceinline__ void k_ipm_dev(DevScalars* sc, const double* USBS_RESTRICT red, int kc,
                                              double alpha, double rho, double mu_tol, int max_iter,
                                              int first_pass) {
@@ -673,24 +998,35 @@ __device__ __forceinline__ void k_ipm_dev(DevScalars* sc, const double* USBS_RES
                   H[j * 8 + l] * G[i * 8 + k] + G[j * 8 + l] * H[i * 8 + k]) * inv_s;
     }
     __syncthreads();
-    if (tid < K) {
-      double f1 = sh.h1[tid] - sh.t[tid] + sh.omega * sh.v[tid] + sh.eta * sh.q12[tid];
-      for (int c = 0; c < K; ++c) f1 += sh.Q[tid * K + c] * sh.s[c];
-      sh.F1[tid] = f1;
+    // The k-sized FP64 chains below are split so that no thread runs a K-long dependent
+    // sequence (one FP64 warp instruction occupies a sub-partition for many cycles):
+    // F1 = Q s + ... with four threads per row (warps 0-4), the scalars in warp 6.
+    if (warp <= 4) {
+      const int r = tid >> 2, h = tid & 3;
+      double f1 = 0.0;
+      if (r < K)
+        for (int c = h; c < K; c += 4) f1 = fma(sh.Q[r * K + c], sh.s[c], f1);
+      f1 += __shfl_xor_sync(FULL, f1, 1);
+      f1 += __shfl_xor_sync(FULL, f1, 2);
+      if (r < K && h == 0)
+        sh.F1[r] = sh.h1[r] - sh.t[r] + sh.omega * sh.v[r] + sh.eta * sh.q12[r] + f1;
     }
-    if (tid == 32) {
-      double trS = 0.0;
-      for (int p = 0; p < kc; ++p) trS += sh.S[p * 8 + p];
-      const double slack = 1.0 - trS - sh.eta;
-      sh.kappa1 = slack / sh.omega;
-      sh.r3 = sh.mu / sh.omega - slack;
-      if (has_eta) {
-        double qs = 0.0;
-        for (int c = 0; c < K; ++c) qs += sh.q12[c] * sh.s[c];
-        const double F2 = qs + sh.eta * sh.q22 + sh.h2 - sh.zeta + sh.omega;
-        sh.kappa2 = sh.zeta / sh.eta + sh.q22;
-        sh.r2 = -F2 + sh.mu / sh.eta - sh.zeta;
-        sh.det = sh.kappa1 * sh.kappa2 + 1.0;
+    if (warp == 6) {
+      double qs = 0.0;
+      for (int c = lane; c < K; c += 32) qs = fma(sh.q12[c], sh.s[c], qs);
+      for (int o = 16; o > 0; o >>= 1) qs += __shfl_xor_sync(FULL, qs, o);
+      if (lane == 0) {
+        double trS = 0.0;
+        for (int p = 0; p < kc; ++p) trS += sh.S[p * 8 + p];
+        const double slack = 1.0 - trS - sh.eta;
+        sh.kappa1 = slack / sh.omega;
+        sh.r3 = sh.mu / sh.omega - slack;
+        if (has_eta) {
+          const double F2 = qs + sh.eta * sh.q22 + sh.h2 - sh.zeta + sh.omega;
+          sh.kappa2 = sh.zeta / sh.eta + sh.q22;
+          sh.r2 = -F2 + sh.mu / sh.eta - sh.zeta;
+          sh.det = sh.kappa1 * sh.kappa2 + 1.0;
+        }
       }
     }
     __syncthreads();
@@ -718,90 +1054,105 @@ __device__ __forceinline__ void k_ipm_dev(DevScalars* sc, const double* USBS_RES
       }
     }
     __syncthreads();
-    // Gaussian elimination with partial pivoting
+    // Gaussian elimination with partial pivoting on [L | rhs].  Rows are addressed through
+    // a permutation instead of being swapped, so warp 0 can look ahead: at pivot p it
+    // updates column p+1 first, picks pivot p+1 and forms its reciprocal while warps
+    // 1.. update columns p+2..K (the rhs included).  One barrier per pivot.
     const int LDL = K + 1;
-    if (tid == 0) sh.piv = 0;
+    int* cur = sh.perm[0];
+    int* nxt = sh.perm[1];
+    if (warp == 0) {
+      if (lane == 0) sh.piv = 0;
+      for (int r = lane; r < K; r += 32) cur[r] = r;
+      __syncwarp();
+      ipm_pivot(sh, cur, cur, 0, K, LDL, lane);
+    }
     __syncthreads();
     for (int p = 0; p < K; ++p) {
-      if (warp == 0) {
-        double best = -1.0;
-        int bi = p;
-        for (int r = p + lane; r < K; r += 32) {
-          const double x = fabs(sh.L[r * LDL + p]);
-          if (x > best) { best = x; bi = r; }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-          const double ob = __shfl_xor_sync(FULL, best, o);
-          const int oi = __shfl_xor_sync(FULL, bi, o);
-          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-        }
-        if (bi != p)
-          for (int c = p + lane; c < LDL; c += 32) {
-            const double x = sh.L[p * LDL + c];
-            sh.L[p * LDL + c] = sh.L[bi * LDL + c];
-            sh.L[bi * LDL + c] = x;
-          }
-        __syncwarp();
-        if (lane == 0) {
-          // an exactly singular system (possible at degenerate optima): mark the
-          // direction unusable instead of dividing by zero
-          const double pv = sh.L[p * LDL + p];
-          sh.fcol[p] = (fabs(pv) > 1e-300) ? 1.0 / pv : 0.0;
-          if (!(fabs(pv) > 1e-300)) sh.piv = -1;
-        }
-      }
-      __syncthreads();
+      const int P = cur[p];
       const double ipv = sh.fcol[p];
-      const int rows = K - p - 1, cols = LDL - p - 1;
-      for (int t = tid; t < rows * cols; t += blockDim.x) {
-        const int r = p + 1 + t / cols, c = p + 1 + t % cols;
-        sh.L[r * LDL + c] -= sh.L[r * LDL + p] * ipv * sh.L[p * LDL + c];
+      if (warp == 0) {
+        if (p + 1 < K) {
+          for (int r = p + 1 + lane; r < K; r += 32) {
+            const int pr = cur[r];
+            const double mult = sh.L[pr * LDL + p] * ipv;
+            sh.L[pr * LDL + p + 1] = fma(-mult, sh.L[P * LDL + p + 1], sh.L[pr * LDL + p + 1]);
+          }
+          __syncwarp();
+          ipm_pivot(sh, cur, nxt, p + 1, K, LDL, lane);
+        }
+      } else {
+        const int nw1 = (blockDim.x >> 5) - 1;
+        for (int r = p + 1 + lane; r < K; r += 32) {
+          const int pr = cur[r];
+          const double mult = sh.L[pr * LDL + p] * ipv;
+          for (int c = p + 1 + warp; c < LDL; c += nw1)
+            sh.L[pr * LDL + c] = fma(-mult, sh.L[P * LDL + c], sh.L[pr * LDL + c]);
+        }
       }
       __syncthreads();
+      if (p + 1 < K) { int* t = cur; cur = nxt; nxt = t; }
     }
-    // back substitution (warp 0) with the reciprocal pivots kept in fcol
+    // back substitution (warp 0) with the reciprocal pivots kept in fcol; row r of the
+    // triangular factor is physical row cur[r]
     if (warp == 0) {
       for (int r = K - 1; r >= 0; --r) {
         double x = 0.0;
         if (lane == 0) {
-          x = sh.L[r * LDL + K] * sh.fcol[r];
+          x = sh.L[cur[r] * LDL + K] * sh.fcol[r];
           sh.ds[r] = x;
         }
         x = __shfl_sync(FULL, x, 0);
-        for (int i = lane; i < r; i += 32) sh.L[i * LDL + K] -= sh.L[i * LDL + r] * x;
+        for (int i = lane; i < r; i += 32) {
+          const int pi = cur[i];
+          sh.L[pi * LDL + K] -= sh.L[pi * LDL + r] * x;
+        }
         __syncwarp();
       }
     }
     __syncthreads();
-    if (tid == 0) {
-      double vds = 0.0;
-      for (int c = 0; c < K; ++c) vds += sh.v[c] * sh.ds[c];
-      if (has_eta) {
-        double qds = 0.0;
-        for (int c = 0; c < K; ++c) qds += sh.q12[c] * sh.ds[c];
+    if (warp == 0) {
+      // v^T ds and q12^T ds by warp reductions, then the scalar directions (lane 0)
+      double vds = 0.0, qds = 0.0;
+      for (int c = lane; c < K; c += 32) {
+        vds = fma(sh.v[c], sh.ds[c], vds);
+        qds = fma(sh.q12[c], sh.ds[c], qds);
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        vds += __shfl_xor_sync(FULL, vds, o);
+        qds += __shfl_xor_sync(FULL, qds, o);
+      }
+      if (lane == 0 && has_eta) {
         const double a = sh.r2 - qds, cc = sh.r3 + vds;
         sh.deta = (sh.kappa1 * a - cc) / sh.det;
         sh.domega = (sh.kappa2 * cc + a) / sh.det;
         sh.dzeta = sh.mu / sh.eta - sh.zeta - (sh.zeta / sh.eta) * sh.deta;
-      } else {
+      } else if (lane == 0) {
         sh.domega = (sh.r3 + vds) / sh.kappa1;
         sh.deta = 0.0;
         sh.dzeta = 0.0;
       }
-    }
-    if (tid >= 32 && tid < 32 + K) {
-      const int r = tid - 32;
-      double x = sh.mu * sh.sinv[r] - sh.t[r];
-      for (int c = 0; c < K; ++c) x -= sh.TS[r * K + c] * sh.ds[c];
-      sh.dt[r] = x;
+    } else if (warp <= 5) {
+      // dt = mu S^-1 - t - (T (x)_s S^-1) ds, four threads per row (warps 1-5)
+      const int r = (tid - 32) >> 2, h = tid & 3;
+      double x = 0.0;
+      if (r < K)
+        for (int c = h; c < K; c += 4) x = fma(sh.TS[r * K + c], sh.ds[c], x);
+      x += __shfl_xor_sync(FULL, x, 1);
+      x += __shfl_xor_sync(FULL, x, 2);
+      if (r < K && h == 0) sh.dt[r] = sh.mu * sh.sinv[r] - sh.t[r] - x;
     }
     __syncthreads();
     // a non-finite Newton direction (singular system): keep the current strictly
     // feasible iterate and stop
-    if (tid == 0) {
-      bool fin = isfinite(sh.deta) && isfinite(sh.domega) && isfinite(sh.dzeta) && sh.piv >= 0;
-      for (int c = 0; c < K && fin; ++c) fin = isfinite(sh.ds[c]) && isfinite(sh.dt[c]);
-      sh.done = fin ? 0 : 2;
+    if (warp == 0) {
+      bool fin = true;
+      for (int c = lane; c < K; c += 32) fin = fin && isfinite(sh.ds[c]) && isfinite(sh.dt[c]);
+      fin = __all_sync(FULL, fin);
+      if (lane == 0) {
+        fin = fin && isfinite(sh.deta) && isfinite(sh.domega) && isfinite(sh.dzeta) && sh.piv >= 0;
+        sh.done = fin ? 0 : 2;
+      }
     }
     __syncthreads();
     if (sh.done == 2) break;
@@ -831,18 +1182,23 @@ __device__ __forceinline__ void k_ipm_dev(DevScalars* sc, const double* USBS_RES
         (void)p; (void)q;
       }
       __syncthreads();
+      // warps 0 and 1 test S and T by Cholesky; warp 2 meanwhile tests the trace slack
+      // and the scalar variables
       bool okw = true;
       if (warp == 0) okw = warp_chol(sh.St, nullptr, kc);
       if (warp == 1) okw = warp_chol(sh.Tt, nullptr, kc);
-      if (lane == 0 && warp < 2) sh.fcol[warp] = okw ? 1.0 : 0.0;
-      __syncthreads();
-      if (tid == 0) {
-        double trS = 0.0;
-        for (int p = 0; p < kc; ++p) trS += sh.St[p * 8 + p];
+      if (warp == 2) {
+        double trS = (lane < kc) ? sh.St[lane * 9] : 0.0;
+        for (int o = 4; o > 0; o >>= 1) trS += __shfl_xor_sync(FULL, trS, o);
         const double en = sh.eta + delta * sh.deta, zn = sh.zeta + delta * sh.dzeta;
         const double on = sh.omega + delta * sh.domega;
-        bool ok = on > 0.0 && (1.0 - trS - en) > 0.0 && sh.fcol[0] > 0.5 && sh.fcol[1] > 0.5;
-        if (has_eta) ok = ok && en > 0.0 && zn > 0.0;
+        okw = on > 0.0 && (1.0 - trS - en) > 0.0;
+        if (has_eta) okw = okw && en > 0.0 && zn > 0.0;
+      }
+      if (lane == 0 && warp < 3) sh.fcol[warp] = okw ? 1.0 : 0.0;
+      __syncthreads();
+      if (tid == 0) {
+        const bool ok = sh.fcol[0] > 0.5 && sh.fcol[1] > 0.5 && sh.fcol[2] > 0.5;
         sh.done = ok ? 1 : 0;
         if (!ok) sh.delta = 0.5 * delta;
       }
@@ -852,38 +1208,36 @@ __device__ __forceinline__ void k_ipm_dev(DevScalars* sc, const double* USBS_RES
     __syncthreads();
     const double delta = 0.95 * sh.delta;
     if (tid < 64) {
+      // each thread reads and writes only its own entry of S and T: in place
       const int p = tid / 8, q = tid % 8;
-      double sv = sh.S[tid], tv = sh.T[tid];
       if (p < kc && q < kc) {
-        sv = sh.S[tid] + 0.5 * delta * (sh.dS[p * 8 + q] + sh.dS[q * 8 + p]);
-        tv = sh.T[tid] + 0.5 * delta * (sh.dT[p * 8 + q] + sh.dT[q * 8 + p]);
+        sh.S[tid] += 0.5 * delta * (sh.dS[p * 8 + q] + sh.dS[q * 8 + p]);
+        sh.T[tid] += 0.5 * delta * (sh.dT[p * 8 + q] + sh.dT[q * 8 + p]);
       }
-      sh.St[tid] = sv;
-      sh.Tt[tid] = tv;
     }
     __syncthreads();
-    if (tid < 64) {
-      sh.S[tid] = sh.St[tid];
-      sh.T[tid] = sh.Tt[tid];
-    }
-    __syncthreads();
-    if (tid == 0) {
-      sh.omega += delta * sh.domega;
-      if (has_eta) {
-        sh.eta += delta * sh.deta;
-        sh.zeta += delta * sh.dzeta;
+    if (warp == 0) {
+      // <S, T> and tr S by warp reductions (entries outside k_c x k_c are zero)
+      double st = fma(sh.S[lane], sh.T[lane], sh.S[lane + 32] * sh.T[lane + 32]);
+      double trS = (lane < kc) ? sh.S[lane * 9] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) {
+        st += __shfl_xor_sync(FULL, st, o);
+        trS += __shfl_xor_sync(FULL, trS, o);
       }
-      double st = 0.0, trS = 0.0;
-      for (int p = 0; p < kc; ++p)
-        for (int q = 0; q < kc; ++q) st += sh.S[p * 8 + q] * sh.T[p * 8 + q];
-      for (int p = 0; p < kc; ++p) trS += sh.S[p * 8 + p];
-      double mest = st + sh.omega * (1.0 - trS - sh.eta);
-      if (has_eta) mest += sh.eta * sh.zeta;
-      mest /= has_eta ? 2.0 * (kc + 2) : 2.0 * (kc + 1);
-      const double gamma = sh.delta * 0.95 <= 0.2 ? 1.0 : 0.5 - 0.4 * delta * delta;
-      sh.mu = fmin(sh.mu, gamma * mest);
-      sh.iters = it;
-      sh.done = (sh.mu < mu_tol || !isfinite(sh.mu)) ? 1 : 0;
+      if (lane == 0) {
+        sh.omega += delta * sh.domega;
+        if (has_eta) {
+          sh.eta += delta * sh.deta;
+          sh.zeta += delta * sh.dzeta;
+        }
+        double mest = st + sh.omega * (1.0 - trS - sh.eta);
+        if (has_eta) mest += sh.eta * sh.zeta;
+        mest /= has_eta ? 2.0 * (kc + 2) : 2.0 * (kc + 1);
+        const double gamma = sh.delta * 0.95 <= 0.2 ? 1.0 : 0.5 - 0.4 * delta * delta;
+        sh.mu = fmin(sh.mu, gamma * mest);
+        sh.iters = it;
+        sh.done = (sh.mu < mu_tol || !isfinite(sh.mu)) ? 1 : 0;
+      }
     }
     __syncthreads();
     if (sh.done) break;
@@ -991,6 +1345,8 @@ __device__ __forceinline__ void k_lanczos_reset_dev(DevLanczos* lz) {
     lz->sweeps = 0;
     lz->status = 0;
     lz->defl = 0;
+    lz->defl_seen = 0;
+    lz->redo = 0;
     lz->converged = 0;
     lz->cycles = 0;
     lz->normest = 0.0;

@@ -458,6 +458,8 @@ static int init_cuda(Ctx* c) {
   USBS_CUDA_TRY(c, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
   const char* dbg = std::getenv("USBS_DEBUG");
   c->debug = dbg && dbg[0] == '1';
+  const char* nospec = std::getenv("USBS_NO_SPECULATE");
+  c->speculate = !(nospec && nospec[0] == '1');
   if (q.stream) {
     c->stream = (cudaStream_t)q.stream;
     c->own_stream = false;
@@ -471,8 +473,12 @@ static int init_cuda(Ctx* c) {
 // ---------------------------------------------------------------------------------------
 // Block Lanczos with CGS2 reorthogonalisation and thick restart
 // ---------------------------------------------------------------------------------------
+// masked = false leaves out the second and third passes (a speculative cycle, rerun with
+// them when the first pass found a deficient column); the random seeds they would have
+// drawn are skipped all the same, so a rerun draws what an unspeculated run draws.
 template <typename T>
-static void orth_block(Ctx* c, T* Q, int nb, T* W, T* out, int j, int write_T, int is_resid) {
+static void orth_block(Ctx* c, T* Q, int nb, T* W, T* out, int j, int write_T, int is_resid,
+                       bool masked = true) {
   const int* defl = DEV_FIELD(c->lz, DevLanczos, defl, int);
   if (nb > 0) {
     const int np = Orth<T>::proj(c, Q, nb, W, nullptr);
@@ -486,6 +492,10 @@ static void orth_block(Ctx* c, T* Q, int nb, T* W, T* out, int j, int write_T, i
   Orth<T>::finalize(c, Q, nb, W, out, nullptr, c->seed + 0x1000003ull * (c->rng_counter++));
   // masked second and third passes: only run when a column was replaced by a random
   // vector (the third zeroes what is still dependent after it)
+  if (!masked) {
+    c->rng_counter += 2;
+    return;
+  }
   const int* defl2 = DEV_FIELD(c->lz, DevLanczos, defl2, int);
   for (int pass = 1; pass <= 2; ++pass) {
     const int* mask = pass == 1 ? defl : defl2;
@@ -551,17 +561,30 @@ static int lanczos(Ctx* c, const double* y_dev, const void* start, void* out_vec
   int matvecs = 0;
   int cycle = 0;
   for (cycle = 0; cycle < c->prm.lanczos_restarts; ++cycle) {
-    for (int j = nb0; j < nblk; ++j) {
-      Bulk<T>::spmm(c, valM, c->dM, Q + j * bs, W);
-      matvecs += 8;
-      orth_block<T>(c, Q, j + 1, W, Q + (j + 1) * bs, j, 1, j == nblk - 1);
-      if (c->debug) debug_block(c, cycle, j);
+    // A cycle first runs speculatively, without the masked passes of its blocks: they are
+    // no-ops unless a first pass finds a deficient column.  If one did, its Rayleigh-Ritz
+    // step left T, Y and the Ritz values untouched and the cycle runs again from the same
+    // state (its kept blocks, T's kept part, the random-seed counter) with the passes.
+    const uint64_t rng0 = c->rng_counter;
+    const int matvecs0 = matvecs;
+    for (int attempt = 0;; ++attempt) {
+      const bool spec = c->speculate && attempt == 0;
+      for (int j = nb0; j < nblk; ++j) {
+        Bulk<T>::spmm(c, valM, c->dM, Q + j * bs, W);
+        matvecs += 8;
+        orth_block<T>(c, Q, j + 1, W, Q + (j + 1) * bs, j, 1, j == nblk - 1, !spec);
+        if (c->debug) debug_block(c, cycle, j);
+      }
+      launch_ritz(c, J, keep, spec ? 1 : 0);
+      USBS_TRY(check_launch(c, "lanczos cycle"));
+      USBS_CUDA_TRY(c, cudaMemcpyAsync(c->h_lz, c->lz, sizeof(DevLanczos), cudaMemcpyDeviceToHost,
+                                       c->stream));
+      USBS_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+      if (!spec || !c->h_lz->redo) break;
+      c->rng_counter = rng0;
+      matvecs = matvecs0;
+      c->spec_redos += 1;
     }
-    launch_ritz(c, J, keep);
-    USBS_TRY(check_launch(c, "lanczos cycle"));
-    USBS_CUDA_TRY(c, cudaMemcpyAsync(c->h_lz, c->lz, sizeof(DevLanczos), cudaMemcpyDeviceToHost,
-                                     c->stream));
-    USBS_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     if (c->h_lz->status == USBS_ETIMEOUT) {
       c->err = "a staged tile copy did not complete within its wait limit";
       return USBS_ETIMEOUT;
@@ -798,6 +821,7 @@ int usbs_extreme_eigs(usbs_ctx* ctx, const double* y, int kc, double* evals, dou
     info->converged = lo.converged;
     info->max_residual = lo.max_res;
     info->jacobi_sweeps = c->h_lz->sweeps;
+    info->reruns = (int)c->spec_redos;
   }
   return USBS_OK;
 }

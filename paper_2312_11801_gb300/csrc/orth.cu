@@ -21,14 +21,14 @@ namespace usbs {
 namespace {
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_tproj(int n, const T* __restrict__ Q, size_t bstride, int nb,
+__global__ void __launch_bounds__(256, 2) k_tproj(int n, const T* __restrict__ Q, size_t bstride, int nb,
                                                const T* __restrict__ W, double* __restrict__ partials,
                                                const int* __restrict__ mask, int* status) {
   k_tproj_dev<T>(blockIdx.x, gridDim.x, n, Q, bstride, nb, W, partials, mask, status);
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_tupdate(int n, const T* __restrict__ Q, size_t bstride, int nb,
+__global__ void __launch_bounds__(256, 2) k_tupdate(int n, const T* __restrict__ Q, size_t bstride, int nb,
                                                  T* __restrict__ W, const double* __restrict__ Hred,
                                                  double* __restrict__ partials,
                                                  const int* __restrict__ mask, int* status) {
@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(256) k_tupdate(int n, const T* __restrict__ Q,
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_tfinalize(int n, const T* __restrict__ Q, size_t bstride,
+__global__ void __launch_bounds__(256, 2) k_tfinalize(int n, const T* __restrict__ Q, size_t bstride,
                                                    int nb, const T* W, const double* __restrict__ H2red,
                                                    const DevLanczos* __restrict__ lz, T* out,
                                                    const int* __restrict__ mask, uint64_t seed, int* status) {
@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(256) k_tfinalize(int n, const T* __restrict__ 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_trestart(int n, const T* __restrict__ Q, size_t bstride, int nbk,
+__global__ void __launch_bounds__(256, 2) k_trestart(int n, const T* __restrict__ Q, size_t bstride, int nbk,
                                                   int nout, const double* __restrict__ Y,
                                                   T* __restrict__ out, size_t ostride,
                                                   const T* __restrict__ resid, int resid_slot, int* status) {

@@ -18,13 +18,24 @@ __global__ void k_chol_block(DevLanczos* lz, const double* __restrict__ red, int
   k_chol_block_dev(lz, red, j, nb, write_T, is_resid, defl_pass, rel_thr);
 }
 
+// spec = 1: the cycle's blocks ran without their masked passes.  If one of them found a
+// deficient column (defl_seen) the basis is not orthonormal: the step is skipped, T, Y and
+// the Ritz values keep their values from the cycle's start, and redo tells the host to run
+// the cycle again with the masked passes.
 template <typename S, int J>
-__global__ void __launch_bounds__(512) k_ritz(DevLanczos* lz, int kc, double tol, int max_sweeps,
-                                              double jac_eps) {
+__global__ void __launch_bounds__(J >= 64 ? 512 : 256, 1) k_ritz(DevLanczos* lz, int kc, double tol, int max_sweeps,
+                                              double jac_eps, int spec) {
+  const int seen = lz->defl_seen;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    lz->defl_seen = 0;
+    lz->redo = (spec && seen) ? 1 : 0;
+  }
+  if (spec && seen) return;
   k_ritz_dev<S, J>(lz, kc, tol, max_sweeps, jac_eps);
 }
 
-__global__ void __launch_bounds__(256) k_ipm(DevScalars* sc, const double* __restrict__ red, int kc,
+__global__ void __launch_bounds__(256, 1) k_ipm(DevScalars* sc, const double* __restrict__ red, int kc,
                                              double alpha, double rho, double mu_tol, int max_iter,
                                              int first_pass) {
   k_ipm_dev(sc, red, kc, alpha, rho, mu_tol, max_iter, first_pass);
@@ -80,28 +91,28 @@ void launch_chol_block(Ctx* c, int j, int nb, int write_T, int is_resid, int def
 }
 
 template <typename S>
-static void launch_ritz_t(Ctx* c, int J, int max_sweeps, double eps) {
+static void launch_ritz_t(Ctx* c, int J, int max_sweeps, double eps, int spec) {
   const size_t sm = ritz_smem(sizeof(S), J);
   const int threads = J >= 64 ? 512 : 256;
   if (J == 16)
-    k_ritz<S, 16><<<1, threads, sm, c->stream>>>(c->lz, c->kc, c->prm.lanczos_tol, max_sweeps, eps);
+    k_ritz<S, 16><<<1, threads, sm, c->stream>>>(c->lz, c->kc, c->prm.lanczos_tol, max_sweeps, eps, spec);
   else if (J == 32)
-    k_ritz<S, 32><<<1, threads, sm, c->stream>>>(c->lz, c->kc, c->prm.lanczos_tol, max_sweeps, eps);
+    k_ritz<S, 32><<<1, threads, sm, c->stream>>>(c->lz, c->kc, c->prm.lanczos_tol, max_sweeps, eps, spec);
   else
-    k_ritz<S, 64><<<1, threads, sm, c->stream>>>(c->lz, c->kc, c->prm.lanczos_tol, max_sweeps, eps);
+    k_ritz<S, 64><<<1, threads, sm, c->stream>>>(c->lz, c->kc, c->prm.lanczos_tol, max_sweeps, eps, spec);
 }
 
-void launch_ritz(Ctx* c, int J, int keep) {
+void launch_ritz(Ctx* c, int J, int keep, int spec) {
   USBS_LAUNCH(c, USBS_KIND_RITZ);
   (void)keep;   // keep = J / 2, fixed by the specialisation
   small_init_attributes();
   if (c->fp64) {
-    launch_ritz_t<double>(c, J, 30, 1e-14);
+    launch_ritz_t<double>(c, J, 30, 1e-14, spec);
   } else {
     // FP32 rotations reach an off-diagonal floor near J * 2^-24 of ||T||: stop at 1e-5.
     // The restart uses the exact projection Y_keep^T T Y_keep, so loose rotations only
     // cost convergence speed, not accuracy.
-    launch_ritz_t<float>(c, J, 12, 1e-5);
+    launch_ritz_t<float>(c, J, 12, 1e-5, spec);
   }
 }
 

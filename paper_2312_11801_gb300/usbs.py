@@ -34,7 +34,8 @@ class usbs_params(ctypes.Structure):
 
 class usbs_eig_info(ctypes.Structure):
     _fields_ = [("cycles", ctypes.c_int), ("matvecs", ctypes.c_int), ("converged", ctypes.c_int),
-                ("max_residual", ctypes.c_double), ("jacobi_sweeps", ctypes.c_int)]
+                ("max_residual", ctypes.c_double), ("jacobi_sweeps", ctypes.c_int),
+                ("reruns", ctypes.c_int)]
 
 
 class usbs_step_info(ctypes.Structure):
