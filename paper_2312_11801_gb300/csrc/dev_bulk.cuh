@@ -232,6 +232,41 @@ __device__ __forceinline__ void svec8(const double* S, double* s) {
       s[bsvec_idx8(p, q)] = (p == q) ? S[p * 8 + q] : 1.41421356237309504880 * S[p * 8 + q];
 }
 
+// Per-constraint products in the bulk type.  In FP32 the 36-term dot <g_c, svec S> is an
+// FP32 dot product and the running sums of G^T w (one term per constraint of the thread)
+// are compensated FP32 sums (Kahan summation): FP64-like accuracy for the sums while the
+// FP64 pipe, a 64th of the FP32 rate on GB300, is left to the few scalars per constraint.
+template <int NV>
+struct KahanSums {
+  float s[NV], c[NV];
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int u = 0; u < NV; ++u) { s[u] = 0.f; c[u] = 0.f; }
+  }
+  __device__ __forceinline__ void add(int u, float x) {
+    const float y = x - c[u];
+    const float t = s[u] + y;
+    c[u] = (t - s[u]) - y;
+    s[u] = t;
+  }
+  __device__ __forceinline__ double value(int u) const { return (double)s[u] - (double)c[u]; }
+};
+
+template <typename T>
+__device__ __forceinline__ double dot_svec(const T (&g)[KSV], const double* ssv, const float* ssf) {
+  if constexpr (sizeof(T) == 4) {
+    float z = 0.f;
+#pragma unroll
+    for (int u = 0; u < KSV; ++u) z = fmaf(g[u], ssf[u], z);
+    return (double)z;
+  } else {
+    double z = 0.0;
+#pragma unroll
+    for (int u = 0; u < KSV; ++u) z += g[u] * ssv[u];
+    return z;
+  }
+}
+
 // ---- candidate: A X_{t+1} = eta A Xbar + G svec(S), y~ = proj_Y(y - (b - A X)/rho) -------
 // partial layout: [0,36) G^T y~, 36 <b,y~>, 37 <A Xbar, y~>, 38 sum d^2, 39 max|d|
 template <typename T>
@@ -248,13 +283,17 @@ __device__ __forceinline__ void k_xupdate_dev(const int cta, const int ncta, int
                                                  double* USBS_RESTRICT ycand,
                                                  double* USBS_RESTRICT partials) {
   __shared__ double ssv[KSV];
+  __shared__ float ssf[KSV];
   __shared__ double sred[8 * 39];
   __shared__ double smax[8];
   __shared__ int finite_ok;
   if (threadIdx.x == 0) {
     svec8(sc->S, ssv);
     int ok = isfinite(sc->eta);
-    for (int u = 0; u < KSV; ++u) ok &= isfinite(ssv[u]);
+    for (int u = 0; u < KSV; ++u) {
+      ok &= isfinite(ssv[u]);
+      ssf[u] = (float)ssv[u];
+    }
     finite_ok = ok;
   }
   __syncthreads();
@@ -267,12 +306,12 @@ __device__ __forceinline__ void k_xupdate_dev(const int cta, const int ncta, int
   double mx = 0.0;
 #pragma unroll
   for (int u = 0; u < 39; ++u) acc[u] = 0.0;
+  KahanSums<KSV> kg;
+  kg.init();
   for (int c = cta * blockDim.x + threadIdx.x; c < m; c += ncta * blockDim.x) {
     T g[KSV];
     build_g<T>(c, con_ptr, ent_i, ent_j, ent_v, V, g);
-    double z = 0.0;
-#pragma unroll
-    for (int u = 0; u < KSV; ++u) z += (double)g[u] * ssv[u];
+    const double z = dot_svec<T>(g, ssv, ssf);
     const double axc = okS ? eta * ax[c] + z : ax[c];
     const double bc = b[c];
     double yc = okS ? y[c] - (bc - axc) * inv_rho : y[c];
@@ -280,14 +319,24 @@ __device__ __forceinline__ void k_xupdate_dev(const int cta, const int ncta, int
     if (iq && yc < 0.0) yc = 0.0;
     axnew[c] = axc;
     ycand[c] = yc;
+    if constexpr (sizeof(T) == 4) {
+      const float ycf = (float)yc;
 #pragma unroll
-    for (int u = 0; u < KSV; ++u) acc[u] += (double)g[u] * yc;
+      for (int u = 0; u < KSV; ++u) kg.add(u, g[u] * ycf);
+    } else {
+#pragma unroll
+      for (int u = 0; u < KSV; ++u) acc[u] += g[u] * yc;
+    }
     acc[36] += bc * yc;
     acc[37] += ax[c] * yc;
     const double proj = iq ? fmin(axc, bc) : bc;
     const double dd = axc - proj;
     acc[38] += dd * dd;
     mx = fmax(mx, fabs(dd));
+  }
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int u = 0; u < KSV; ++u) acc[u] = kg.value(u);
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
@@ -317,20 +366,24 @@ __device__ __forceinline__ void k_alt_dev(const int cta, const int ncta, int m, 
                                              double alpha, double* USBS_RESTRICT nu,
                                              double* USBS_RESTRICT partials) {
   __shared__ double ssv[KSV];
+  __shared__ float ssf[KSV];
   __shared__ double sred[8 * 38];
-  if (threadIdx.x == 0) svec8(sc->S_hat, ssv);
+  if (threadIdx.x == 0) {
+    svec8(sc->S_hat, ssv);
+    for (int u = 0; u < KSV; ++u) ssf[u] = (float)ssv[u];
+  }
   __syncthreads();
   const double coef = sc->has_eta ? sc->eta_hat / sc->tr : 0.0;
   const double inv_rho = 1.0 / rho;
   double acc[38];
 #pragma unroll
   for (int u = 0; u < 38; ++u) acc[u] = 0.0;
+  KahanSums<KSV> kg;
+  kg.init();
   for (int c = cta * blockDim.x + threadIdx.x; c < m; c += ncta * blockDim.x) {
     T g[KSV];
     build_g<T>(c, con_ptr, ent_i, ent_j, ent_v, V, g);
-    double z = 0.0;
-#pragma unroll
-    for (int u = 0; u < KSV; ++u) z += (double)g[u] * ssv[u];
+    const double z = dot_svec<T>(g, ssv, ssf);
     const double axt = alpha * (coef * ax[c] + z);
     const double bc = b[c];
     double nn = 0.0;
@@ -338,10 +391,20 @@ __device__ __forceinline__ void k_alt_dev(const int cta, const int ncta, int m, 
     const double dn = nn - nu[c];
     nu[c] = nn;
     const double wc = y[c] - (bc - nn) * inv_rho;
+    if constexpr (sizeof(T) == 4) {
+      const float wcf = (float)wc;
 #pragma unroll
-    for (int u = 0; u < KSV; ++u) acc[u] += (double)g[u] * wc;
+      for (int u = 0; u < KSV; ++u) kg.add(u, g[u] * wcf);
+    } else {
+#pragma unroll
+      for (int u = 0; u < KSV; ++u) acc[u] += g[u] * wc;
+    }
     acc[36] += ax[c] * wc;
     acc[37] += dn * dn;
+  }
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int u = 0; u < KSV; ++u) acc[u] = kg.value(u);
   }
   block_reduce_store<38>(cta, acc, partials, sred);
 }
@@ -353,15 +416,16 @@ __device__ __forceinline__ void k_constraint_eval_dev(const int cta, const int n
                                   const T* USBS_RESTRICT V, const double* USBS_RESTRICT S,
                                   double* USBS_RESTRICT z) {
   __shared__ double ssv[KSV];
-  if (threadIdx.x == 0) svec8(S, ssv);
+  __shared__ float ssf[KSV];
+  if (threadIdx.x == 0) {
+    svec8(S, ssv);
+    for (int u = 0; u < KSV; ++u) ssf[u] = (float)ssv[u];
+  }
   __syncthreads();
   for (int c = cta * blockDim.x + threadIdx.x; c < m; c += ncta * blockDim.x) {
     T g[KSV];
     build_g<T>(c, con_ptr, ent_i, ent_j, ent_v, V, g);
-    double s = 0.0;
-#pragma unroll
-    for (int u = 0; u < KSV; ++u) s += (double)g[u] * ssv[u];
-    z[c] = s;
+    z[c] = dot_svec<T>(g, ssv, ssf);
   }
 }
 
