@@ -61,41 +61,6 @@ __device__ bool warp_chol(const double* A, double* R, int k) {
   return true;
 }
 
-// Inverse of an SPD k x k matrix from its upper Cholesky factor R (row stride 8):
-// A^-1 = R^-1 R^-T.  Warp-cooperative; Rinv is scratch (row stride 8).
-__device__ void warp_spd_inverse(const double* R, double* Rinv, double* Ainv, int k) {
-  const int lane = threadIdx.x & 31;
-  // reciprocals of the diagonal, one per lane, shared by shuffles: the back substitution
-  // then multiplies instead of dividing at every step of its serial chain
-  const double rd_own = (lane < k) ? 1.0 / R[lane * 8 + lane] : 0.0;
-  double rd[8];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) rd[i] = __shfl_sync(FULL, rd_own, i);
-  if (lane < k) {
-    const int c = lane;
-    double x[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) x[i] = 0.0;
-    x[c] = rd[c];
-    for (int i = c - 1; i >= 0; --i) {
-      double sacc = 0.0;
-      for (int l = i + 1; l <= c; ++l) sacc += R[i * 8 + l] * x[l];
-      x[i] = -sacc * rd[i];
-    }
-#pragma unroll
-    for (int i = 0; i < 8; ++i) Rinv[i * 8 + c] = (i < k) ? x[i] : 0.0;
-  }
-  __syncwarp();
-  for (int t = lane; t < 64; t += 32) {
-    const int i = t / 8, j = t % 8;
-    double v = 0.0;
-    if (i < k && j < k)
-      for (int l = 0; l < k; ++l) v += Rinv[i * 8 + l] * Rinv[j * 8 + l];
-    Ainv[t] = v;
-  }
-  __syncwarp();
-}
-
 // Largest eigenvalue of a small symmetric matrix (k <= 8, row stride 8): parallel
 // Jacobi in FP32 by one warp for the eigenvector, then its FP64 Rayleigh quotient.
 __device__ double warp_lambda_max(const double* A, int k, float* Af, float* Vf) {
@@ -845,13 +810,50 @@ __device__ __forceinline__ void k_ritz_dev(DevLanczos* lz, int kc, double tol, i
 }
 
 // ---- App. B.2 interior point method --------------------------------------------------------
+// S^-1 for the symmetric positive definite k_c x k_c block of S (an 8 x 8 array) by
+// Gauss-Jordan elimination of [S | I] without pivoting (the pivots of an SPD matrix are
+// positive).  Threads 0..127 own the 128 entries of [S | I], double-buffered in buf
+// (256 doubles), one barrier per pivot; every thread of the CTA calls it.  Each pivot costs
+// one FP64 reciprocal and one fused update per entry, all entries at once: a warp-serial
+// Cholesky, triangular inverse and product took about seven times as long on GB300's FP64
+// rate.  The result is symmetrised; entries outside the k_c x k_c block are the identity's.
+__device__ __forceinline__ void cta_spd_inverse8(const double* S, double* buf, double* Sinv, int kc) {
+  const int tid = threadIdx.x;
+  const int r = (tid >> 4) & 7, c = tid & 15;
+  double* cur = buf;
+  double* nxt = buf + 128;
+  if (tid < 128) {
+    double v;
+    if (c < 8) v = (r < kc && c < kc) ? S[r * 8 + c] : (r == c ? 1.0 : 0.0);
+    else v = (c - 8 == r) ? 1.0 : 0.0;
+    cur[tid] = v;
+  }
+  __syncthreads();
+  for (int p = 0; p < kc; ++p) {
+    if (tid < 128) {
+      const double ip = 1.0 / cur[p * 16 + p];
+      const double mpc = cur[p * 16 + c] * ip;
+      nxt[tid] = (r == p) ? mpc : fma(-cur[r * 16 + p], mpc, cur[tid]);
+    }
+    __syncthreads();
+    double* t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+  if (tid < 64) {
+    const int i = tid >> 3, j = tid & 7;
+    Sinv[tid] = 0.5 * (cur[i * 16 + 8 + j] + cur[j * 16 + 8 + i]);
+  }
+  __syncthreads();
+}
+
 struct IpmShared {
   double Q[KSV * KSV];
   double TS[KSV * KSV];
   double L[KSV * (KSV + 1)];
   double q12[KSV], h1[KSV], v[KSV], s[KSV], t[KSV], sinv[KSV], F1[KSV], ds[KSV], dt[KSV];
   double fcol[KSV];
-  double S[64], T[64], Sinv[64], Lc[64], work[64], dS[64], dT[64], St[64], Tt[64];
+  double S[64], T[64], Sinv[64], dS[64], dT[64], St[64], Tt[64];
   double q22, h2, eta, zeta, omega, mu, deta, dzeta, domega, delta, kappa1, kappa2, det, r2, r3;
   int map[KSV];
   int perm[2][KSV];            // row permutations of the elimination (current, next)
@@ -962,12 +964,9 @@ __device__ __forceinline__ void k_ipm_dev(DevScalars* sc, const double* USBS_RES
   __syncthreads();
   const int lane = tid & 31, warp = tid >> 5;
   for (int it = 1; it <= max_iter; ++it) {
-    // S^-1 (warp-cooperative Cholesky and inverse)
-    if (warp == 0) {
-      warp_chol(sh.S, sh.Lc, kc);
-      warp_spd_inverse(sh.Lc, sh.work, sh.Sinv, kc);
-    }
-    __syncthreads();
+    // S^-1 (Gauss-Jordan over the CTA; the system matrix L is assembled later, so its
+    // storage serves as the scratch)
+    cta_spd_inverse8(sh.S, sh.L, sh.Sinv, kc);
     if (tid < K) {
       int p = 0, q = 0;
       int u = tid;
@@ -1094,20 +1093,17 @@ __device__ __forceinline__ void k_ipm_dev(DevScalars* sc, const double* USBS_RES
       if (p + 1 < K) { int* t = cur; cur = nxt; nxt = t; }
     }
     // back substitution (warp 0) with the reciprocal pivots kept in fcol; row r of the
-    // triangular factor is physical row cur[r]
+    // triangular factor is physical row cur[r].  Lane i keeps the right-hand sides of rows
+    // i and i + 32 in registers, so a step is a shuffle, a multiply and a fused update.
     if (warp == 0) {
+      double y0 = (lane < K) ? sh.L[cur[lane] * LDL + K] : 0.0;
+      double y1 = (lane + 32 < K) ? sh.L[cur[lane + 32] * LDL + K] : 0.0;
       for (int r = K - 1; r >= 0; --r) {
-        double x = 0.0;
-        if (lane == 0) {
-          x = sh.L[cur[r] * LDL + K] * sh.fcol[r];
-          sh.ds[r] = x;
-        }
-        x = __shfl_sync(FULL, x, 0);
-        for (int i = lane; i < r; i += 32) {
-          const int pi = cur[i];
-          sh.L[pi * LDL + K] -= sh.L[pi * LDL + r] * x;
-        }
-        __syncwarp();
+        const double yr = __shfl_sync(FULL, r < 32 ? y0 : y1, r & 31);
+        const double x = yr * sh.fcol[r];
+        if (lane == 0) sh.ds[r] = x;
+        if (lane < r) y0 = fma(-sh.L[cur[lane] * LDL + r], x, y0);
+        if (lane + 32 < r) y1 = fma(-sh.L[cur[lane + 32] * LDL + r], x, y1);
       }
     }
     __syncthreads();
