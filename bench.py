@@ -254,6 +254,17 @@ def run_ours(args, world, rank, local, pg):
     # (J = 64, 50 restarts): a Ritz value never exceeds lambda_max, so this check is a
     # floor under the true f(y).
     last = results[-1]["last"]
+    # rank-r reconstruction of the final primal from its sketch and the best rounded cut
+    # (App. C, App. E), timed on its own outside the solve's timed region
+    torch.cuda.synchronize()
+    tn = time.perf_counter()
+    try:
+        lam_ny, _, cut_vals, cut_best, _ = U.usbs_nystrom_round(ctx, want_u=False, want_signs=False)
+        nystrom = {"ms": 1e3 * (time.perf_counter() - tn), "r": R_SKETCH, "lam_top": float(lam_ny[0]),
+                   "rounded_cut": float(cut_vals[cut_best]),
+                   "rounded_over_objective": float(cut_vals[cut_best]) / last["objective"]}
+    except U.USBSError as exc:
+        nystrom = {"error": str(exc)}
     y_fin = U.usbs_get_dual(ctx)
     c_scale, tau = U.usbs_scaling(ctx)
     with U.usbs_create(prob, lanczos_basis=64, lanczos_restarts=50, lanczos_tol=1e-8,
@@ -297,6 +308,7 @@ def run_ours(args, world, rank, local, pg):
                      if dom == "reorth_update" and nl else None,
                      "algorithmic_bytes_per_launch": by / nl if nl else None,
                      "peak_source": peak_src},
+        "nystrom": nystrom,
         "lanczos_spmm": {"achieved_gbs": spmm_gbs, "frac": spmm_gbs / hbm, "launches": spmm_n,
                          "avg_us": 1e3 * spmm_ms / max(spmm_n, 1),
                          "bytes_per_launch": spmm_b / max(spmm_n, 1)},

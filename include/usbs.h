@@ -34,7 +34,7 @@
 extern "C" {
 #endif
 
-#define USBS_ABI_VERSION 1
+#define USBS_ABI_VERSION 2   /* 2: usbs_eig_info.reruns, usbs_nystrom_round */
 
 /* status codes */
 #define USBS_OK          0
@@ -180,6 +180,27 @@ int usbs_solve(usbs_ctx* ctx, int warm_start, double tol, usbs_result* out);
  *  P       : n x r FP32 host, X Psi (may be NULL),  Psi : n x r FP32 host (may be NULL),
  *  scalars : 2 FP64 host {<C, Xbar>, tr Xbar} (may be NULL). */
 int usbs_get_sketch(usbs_ctx* ctx, float* P, float* Psi, double* scalars);
+
+/*
+ * usbs_nystrom_round -- rank-r reconstruction of the primal from its sketch and MaxCut
+ * rounding (App. C, eq. nystrom_approx; App. E, rounding).
+ * From the context's sketch P = Xbar Psi and test matrix Psi (n x r), by the stable method
+ * of Tropp, Yurtsever, Udell and Cevher (2017, Algorithm 3):
+ *   nu = sqrt(n) eps(||P||_2) with eps the FP32 spacing (the sketch is stored in FP32),
+ *   Y = P + nu Psi, Psi^T Y = R^T R, Y R^-1 = U Sigma W^T, lam = max(Sigma^2 - nu, 0),
+ * so that X_hat = U diag(lam) U^T approximates Xbar in the problem's units.  Every column
+ * u_k of U gives the sign vector z_k = sgn(u_k) (0 counted as +1), valued <C, z_k z_k^T>
+ * (for C = L/4 the weight of the cut z_k); the best column is reported.
+ *   lam    : r FP64 host, descending (required).
+ *   U      : n x r FP64 host, row-major, orthonormal columns; NULL to skip the copy.
+ *   values : r FP64 host, the value of every column's sign vector; may be NULL.
+ *   best   : host int, the index of the column with the largest value; may be NULL.
+ *   signs  : n int8 host, the best column's sign vector (+1 / -1); may be NULL.
+ * Computed on the device in FP64 from the FP32 sketch; allocates n x r doubles of scratch
+ * for the call.  Errors: USBS_EINVAL without a sketch (r = 0), USBS_ENUMERIC if Psi^T Y is
+ * not positive definite, USBS_ECUDA / USBS_ENOMEM from the device.
+ */
+int usbs_nystrom_round(usbs_ctx* ctx, double* lam, double* U, double* values, int* best, int8_t* signs);
 
 /* Current dual iterate y_t (m FP64 host), problem units. */
 int usbs_get_dual(usbs_ctx* ctx, double* y);

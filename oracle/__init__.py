@@ -14,6 +14,8 @@ Modules
 ``ipm``    App. B.2 primal-dual interior point method for eq. compressed_subprob_2;
            App. B.1 as its special case with zero quadratic data; the closed form of
            the model value.
+``nystrom`` the stable Nystrom reconstruction of the primal from its sketch (App. C,
+           eq. nystrom_approx; Tropp et al. 2017, Algorithm 3) and MaxCut rounding (App. E).
 ``usbs``   problem scaling (App. E), the operators A, A*, the USBS iteration
            (Algorithm 1, Sec. 3) with the implicit primal and the Nystrom sketch
            (Sec. 4, App. C), the stopping gates (eq. relative_error_tol) and solve.

@@ -106,6 +106,8 @@ SIGNATURES = [
     ("usbs_step", ctypes.c_int, [_P, ctypes.POINTER(usbs_step_info)]),
     ("usbs_solve", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.POINTER(usbs_result)]),
     ("usbs_get_sketch", ctypes.c_int, [_P, _F, _F, _D]),
+    ("usbs_nystrom_round", ctypes.c_int, [_P, _D, _D, _D, ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_int8)]),
     ("usbs_get_dual", ctypes.c_int, [_P, _D]),
     ("usbs_get_primal_constraints", ctypes.c_int, [_P, _D]),
     ("usbs_state_size", ctypes.c_int64, [_P]),
@@ -291,6 +293,22 @@ def usbs_get_sketch(ctx):
     _check(load().usbs_get_sketch(ctx.ptr, _ptr(P, ctypes.c_float), _ptr(Psi, ctypes.c_float),
                                   _ptr(sc, ctypes.c_double)), ctx.ptr)
     return P, Psi, sc
+
+
+def usbs_nystrom_round(ctx, want_u=True, want_signs=True):
+    """Rank-r reconstruction X_hat = U diag(lam) U^T of the primal from the sketch and the
+    best sign-vector cut over the columns of U (problem units).  Returns
+    (lam, U or None, values, best, signs or None)."""
+    lam = np.zeros(ctx.r)
+    vals = np.zeros(ctx.r)
+    U = np.zeros((ctx.n, ctx.r)) if want_u else None
+    z = np.zeros(ctx.n, np.int8) if want_signs else None
+    best = ctypes.c_int(-1)
+    _check(load().usbs_nystrom_round(ctx.ptr, _ptr(lam, ctypes.c_double),
+                                     None if U is None else _ptr(U, ctypes.c_double),
+                                     _ptr(vals, ctypes.c_double), ctypes.byref(best),
+                                     None if z is None else _ptr(z, ctypes.c_int8)), ctx.ptr)
+    return lam, U, vals, best.value, z
 
 
 def usbs_get_dual(ctx):
