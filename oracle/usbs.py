@@ -18,7 +18,14 @@ which the candidate of eq. dual_update equals proj_Y(y - (b - A X)/rho), is
 complementary to nu and keeps y_I >= 0, as Sec. 3 states; the printed "nu_I <= 0" would
 give y_I <= 0.
 
-k_p = 0 throughout (Xbar = X, V_{t+1} = [v_1..v_kc]), as in the configurations built.
+k_p = 0 by default (Xbar = X, V_{t+1} = [v_1..v_kc]), as in the configurations built.
+With k_p > 0 (Sec. 3, eqs. model_update_eigendecomposition, x_bar_def, v_next_def) V has
+k_c + k_p columns; S_{t+1} = Q_p L_p Q_p^T + Q_c L_c Q_c^T splits off its k_p largest
+eigenpairs as past information, Xbar_{t+1} = eta Xbar_t + V Q_c L_c Q_c^T V^T takes only
+the rest, and V_{t+1} is an orthonormal basis (QR) of [V Q_p, v_1..v_kc].  The primal
+iterate X_{t+1} = eta Xbar_t + V S V^T then differs from Xbar_{t+1}; the gates and the
+objective are X_{t+1}'s, the model and the sketch Xbar's.  The cold start takes the top
+k_c + k_p eigenvectors of C as V_0.
 """
 import dataclasses
 import math
@@ -138,18 +145,23 @@ class State:
     P: np.ndarray             # Xbar Psi (n x r), r may be 0
     Xbar: np.ndarray = None   # dense Xbar, only when tracked (tiny n)
     t: int = 0
+    cx_it: float = 0.0        # <C, X_t> of the primal iterate (= cx when k_p = 0)
+    ax_it: np.ndarray = None  # A X_t (= ax when k_p = 0)
+    X: np.ndarray = None      # dense X_t, only when tracked
 
 
 class USBSOracle:
-    """One USBS instance (Algorithm 1), FP64, k_p = 0."""
+    """One USBS instance (Algorithm 1), FP64.  k = k_c current eigenvectors, k_p past
+    columns (default 0)."""
 
     def __init__(self, prob, k=8, rho=0.01, beta=0.25, alpha=2.0, psi=None,
                  ipm_mu_tol=1e-7, max_alt=50, alt_tol=1e-8, eig_tol=1e-10,
-                 dense_track=False, seed=0):
+                 dense_track=False, seed=0, k_p=0):
         self.prob = prob
         self.sp = scale_problem(prob)
         k = min(k, prob.n)
         self.k, self.rho, self.beta, self.alpha = k, rho, beta, alpha
+        self.k_p = max(0, min(int(k_p), prob.n - k))
         self.psi = None if psi is None else np.asarray(psi, dtype=np.float64)
         self.ipm_mu_tol, self.max_alt, self.alt_tol = ipm_mu_tol, max_alt, alt_tol
         self.eig_tol = eig_tol
@@ -168,14 +180,20 @@ class USBSOracle:
         return self.alpha * max(lam_max, 0.0) + float(self.sp.b @ y)
 
     def cold_start(self):
-        """y_0 = 0, Xbar_0 = 0 (tr Xbar_0 = 0), V_0 = top-k eigenvectors of C."""
+        """y_0 = 0, Xbar_0 = 0 (tr Xbar_0 = 0), V_0 = top-(k_c + k_p) eigenvectors of C."""
         n, m = self.sp.n, self.sp.m
         y = np.zeros(m)
-        w, U = self.eig_at(y)
+        if self.k_p:
+            w, U = top_eigenpairs(slack_matrix(self.sp, y), self.k + self.k_p, tol=self.eig_tol,
+                                  seed=self.seed)
+        else:
+            w, U = self.eig_at(y)
         r = 0 if self.psi is None else self.psi.shape[1]
         self.state = State(y=y, V=U, f_y=self.f_value(w[0], y), cx=0.0, tr=0.0,
                            ax=np.zeros(m), P=np.zeros((n, r)),
-                           Xbar=np.zeros((n, n)) if self.dense_track else None)
+                           Xbar=np.zeros((n, n)) if self.dense_track else None,
+                           cx_it=0.0, ax_it=np.zeros(m),
+                           X=np.zeros((n, n)) if self.dense_track else None)
         return self.state
 
     def model_data(self, st):
@@ -212,9 +230,10 @@ class USBSOracle:
         any_ineq = bool(np.any(sp_.ineq))
         n_alt = 0
         ipm_iters = 0
+        kv = st.V.shape[1]                    # k_c + k_p columns
         for n_alt in range(1, self.max_alt + 1):
             h1, h2 = self.linear_data(st, Vc, G, has_eta, nu)
-            sol = ipm_quad(Q11, q12, q22, h1, h2, k, has_eta, self.ipm_mu_tol)
+            sol = ipm_quad(Q11, q12, q22, h1, h2, kv, has_eta, self.ipm_mu_tol)
             ipm_iters += sol["iters"]
             S_hat, eta_hat = sol["S"], sol["eta"]
             if not any_ineq:
@@ -233,7 +252,7 @@ class USBSOracle:
         trX = eta * st.tr + float(np.trace(S))
         # candidate, eq. dual_update in its projected form
         y_new = proj_Y(sp_, st.y - (sp_.b - AX) / rho)
-        w, U = self.eig_at(y_new, start=st.V)
+        w, U = self.eig_at(y_new, start=st.V[:, :k])
         f_new = self.f_value(w[0], y_new)
         # model value f_hat_t(y_new) (App. B.1, closed form)
         VZV = Vc - smat(G.T @ y_new)
@@ -243,13 +262,35 @@ class USBSOracle:
         descent = self.beta * (f_old - f_hat) <= f_old - f_new
         if descent:
             st.y, st.f_y = y_new, f_new
-        # model update with k_p = 0: Xbar_{t+1} = X_{t+1}; sketch; V_{t+1}
-        if st.P.shape[1]:
-            st.P = eta * st.P + st.V @ (S @ (st.V.T @ self.psi))
-        if st.Xbar is not None:
-            st.Xbar = eta * st.Xbar + st.V @ S @ st.V.T
-        st.cx, st.tr, st.ax = CX, trX, AX
-        st.V = U
+        if st.X is not None:
+            st.X = eta * st.Xbar + st.V @ S @ st.V.T
+        st.cx_it, st.ax_it = CX, AX
+        if self.k_p == 0:
+            # model update with k_p = 0: Xbar_{t+1} = X_{t+1}; sketch; V_{t+1}
+            if st.P.shape[1]:
+                st.P = eta * st.P + st.V @ (S @ (st.V.T @ self.psi))
+            if st.Xbar is not None:
+                st.Xbar = eta * st.Xbar + st.V @ S @ st.V.T
+            st.cx, st.tr, st.ax = CX, trX, AX
+            st.V = U
+        else:
+            # eq. model_update_eigendecomposition: the k_p largest eigenpairs of S are the
+            # past part, the remaining k_c the current part
+            lam, Qs = np.linalg.eigh(0.5 * (S + S.T))
+            order = np.argsort(-lam, kind="stable")
+            lam, Qs = lam[order], Qs[:, order]
+            Qp, Qc, Lc = Qs[:, :self.k_p], Qs[:, self.k_p:], lam[self.k_p:]
+            Sc = (Qc * Lc) @ Qc.T
+            # eq. x_bar_def through its implicit quantities (App. C)
+            st.cx = eta * st.cx + float(np.sum(Vc * Sc))
+            st.tr = eta * st.tr + float(np.sum(Lc))
+            st.ax = eta * st.ax + A_lowrank(sp_, st.V, Sc)
+            if st.P.shape[1]:
+                st.P = eta * st.P + st.V @ (Sc @ (st.V.T @ self.psi))
+            if st.Xbar is not None:
+                st.Xbar = eta * st.Xbar + st.V @ Sc @ st.V.T
+            # eq. v_next_def: an orthonormal basis of [V Q_p, v_1..v_kc] by QR
+            st.V, _ = np.linalg.qr(np.hstack([st.V @ Qp, U]))
         st.t += 1
         relgap, relinf = self.gates(st)
         return {"t": st.t, "descent": bool(descent), "f_y": st.f_y, "f_cand": f_new,
@@ -259,9 +300,12 @@ class USBSOracle:
                 "relgap": relgap, "relinf": relinf, "AX": AX}
 
     def gates(self, st):
-        """Relative suboptimality bound and relative infeasibility (App. E), scaled units."""
-        relgap = abs(st.f_y - st.cx) / (1.0 + abs(st.cx))
-        relinf = float(np.linalg.norm(st.ax - proj_K(self.sp, st.ax))) / (1.0 + self.bnorm)
+        """Relative suboptimality bound and relative infeasibility (App. E) of the primal
+        iterate X_t, scaled units."""
+        cx = st.cx_it if self.k_p else st.cx
+        ax = st.ax_it if self.k_p else st.ax
+        relgap = abs(st.f_y - cx) / (1.0 + abs(cx))
+        relinf = float(np.linalg.norm(ax - proj_K(self.sp, ax))) / (1.0 + self.bnorm)
         return relgap, relinf
 
     def solve(self, tol=1e-3, max_iters=1000, callback=None):
@@ -279,7 +323,8 @@ class USBSOracle:
 
     # results in the units of the unscaled problem
     def objective(self):
-        return self.state.cx * self.sp.c_scale * self.sp.tau
+        cx = self.state.cx_it if self.k_p else self.state.cx
+        return cx * self.sp.c_scale * self.sp.tau
 
     def dual_bound(self):
         return self.state.f_y * self.sp.c_scale * self.sp.tau
