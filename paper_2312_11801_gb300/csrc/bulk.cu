@@ -130,14 +130,6 @@ void reduce_partials(Ctx* c, int nparts, int nvals, double* out, const int* mask
   k_reduce<<<(nvals + 31) / 32, 256, 0, c->stream>>>(c->partials, nparts, nvals, out, mask);
 }
 
-// CTAs for kernels whose CTA covers 32 rows per iteration (8 warps x 4 rows)
-static int row32_grid(Ctx* c, int64_t n) {
-  int64_t g = (n + 31) / 32;
-  const int64_t cap = (int64_t)c->num_sms * 8;
-  if (g > cap) g = cap;
-  return (int)(g < 1 ? 1 : g);
-}
-
 // algorithmic bytes of a per-constraint kernel: each entry (i, j, value) and con_ptr once,
 // V once, and `per_row` bytes of FP64 m-vectors per constraint
 static double constr_bytes(Ctx* c, double es, double per_row) {
