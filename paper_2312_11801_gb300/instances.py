@@ -28,7 +28,7 @@ import numpy as np
 __all__ = [
     "Problem", "laplacian_maxcut", "maxcut_er", "maxcut_torus", "maxcut_rgg",
     "grow_rgg", "clustering_sdp", "maxcut_from_edges", "complete_graph_edges",
-    "cycle_edges", "batched_er", "gaussian_psi", "save_npz", "load_npz",
+    "cycle_edges", "batched_er", "qap_sdp", "gaussian_psi", "save_npz", "load_npz",
 ]
 
 
@@ -255,6 +255,86 @@ def clustering_sdp(n=65536, n_edges=655360, seed=0) -> Problem:
     return Problem(n, rowptr, col, val, A_con, A_i, A_j, A_val, b, ineq, float(n),
                    name=f"clustering_n{n}_e{n_edges}_s{seed}",
                    meta={"n_edges": n_edges, "seed": seed})
+
+
+def qap_sdp(nq=6, seed=0) -> Problem:
+    """Synthetic QAP relaxation in the form of App. E (QAP, eq. qap_sdp), for minimising
+    tr(W Pi D Pi^T) over permutations Pi of nq items.
+
+    W (flows) is a ring over the nq facilities plus nq/2 random chords, integer weights
+    1..4; D (distances) is the Manhattan distance between nq random points of a
+    nq x nq grid.  X = [[1, vec(B)^T], [vec(B), Y]] has n = nq^2 + 1 rows; index
+    1 + i + nq j holds B_ij (vec stacks columns), so Y's Kronecker order matches D (x) W.
+    The objective is maximised as <C, X> with C = -(D (x) W) on the Y block.  Rows:
+      0                      X_00 = 1
+      tr_1(Y) = I            sum_j Y[(i1, j), (i2, j)] = delta_i1i2, i1 <= i2
+      tr_2(Y) = I            sum_i Y[(i, j1), (i, j2)] = delta_j1j2, j1 <= j2
+      vec(B) = diag(Y)       X_{0, p} - X_{p, p} = 0 for every p
+      B 1 = 1, 1^T B = 1^T   row and column sums of B
+      tr(Y) = nq
+      G(Y) >= 0              -Y_pq <= 0 on the support of D (x) W (inequalities)
+      B >= 0                 -X_{0, p} <= 0 (inequalities)
+    tr X* = 1 + nq (X_00 = 1 and tr Y = nq).
+    """
+    rng = np.random.Generator(np.random.PCG64(20_000 + seed))
+    W = np.zeros((nq, nq))
+    for a in range(nq):
+        b_ = (a + 1) % nq
+        W[a, b_] = W[b_, a] = rng.integers(1, 5)
+    for _ in range(nq // 2):
+        a, b_ = rng.choice(nq, size=2, replace=False)
+        W[a, b_] = W[b_, a] = rng.integers(1, 5)
+    pts = rng.choice(nq * nq, size=nq, replace=False)
+    px, py = pts % nq, pts // nq
+    D = (np.abs(px[:, None] - px[None, :]) + np.abs(py[:, None] - py[None, :])).astype(np.float64)
+    n = nq * nq + 1
+    K = np.kron(D, W)                     # K[j1 nq + i1, j2 nq + i2] = D[j1, j2] W[i1, i2]
+    rr, cc = np.nonzero(np.triu(K, 1))
+    rows = np.concatenate([rr + 1, cc + 1])
+    cols = np.concatenate([cc + 1, rr + 1])
+    vals = np.concatenate([-K[rr, cc], -K[rr, cc]])
+    order = np.lexsort((cols, rows))
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    rowptr = np.zeros(n + 1, np.int64)
+    np.add.at(rowptr, rows + 1, 1)
+    rowptr = np.cumsum(rowptr)
+    con, ai, aj, av, bb, iq = [], [], [], [], [], []
+
+    def row(entries, rhs, ineq=0):
+        c = len(bb)
+        for (i, j, v) in entries:
+            con.append(c)
+            ai.append(min(i, j))
+            aj.append(max(i, j))
+            av.append(v)
+        bb.append(rhs)
+        iq.append(ineq)
+
+    def y(i, j):                          # index of B_ij / of Y's row (i, j)
+        return 1 + i + nq * j
+
+    row([(0, 0, 1.0)], 1.0)
+    for i1 in range(nq):
+        for i2 in range(i1, nq):
+            row([(y(i1, j), y(i2, j), 1.0) for j in range(nq)], 1.0 if i1 == i2 else 0.0)
+    for j1 in range(nq):
+        for j2 in range(j1, nq):
+            row([(y(i, j1), y(i, j2), 1.0) for i in range(nq)], 1.0 if j1 == j2 else 0.0)
+    for p in range(1, n):
+        row([(0, p, 1.0), (p, p, -1.0)], 0.0)
+    for i in range(nq):
+        row([(0, y(i, j), 1.0) for j in range(nq)], 1.0)
+    for j in range(nq):
+        row([(0, y(i, j), 1.0) for i in range(nq)], 1.0)
+    row([(p, p, 1.0) for p in range(1, n)], float(nq))
+    for a, b_ in zip(rr, cc):
+        row([(a + 1, b_ + 1, -1.0)], 0.0, 1)
+    for p in range(1, n):
+        row([(0, p, -1.0)], 0.0, 1)
+    return Problem(n, rowptr, cols.astype(np.int32), vals, np.asarray(con, np.int32),
+                   np.asarray(ai, np.int32), np.asarray(aj, np.int32), np.asarray(av, np.float64),
+                   np.asarray(bb, np.float64), np.asarray(iq, np.uint8), float(1 + nq),
+                   name=f"qap_n{nq}_s{seed}", meta={"nq": nq, "W": W, "D": D})
 
 
 def batched_er(count=512, n_lo=100, n_hi=4000, avg_deg=8.0, seed0=0):
