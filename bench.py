@@ -126,10 +126,13 @@ def barrier(pg):
 
 
 def max_over_ranks(pg, x):
+    """The largest x over the ranks (the timing rule: max over ranks).  NCCL reduces a
+    device tensor, gloo (the CPU tests of this path) a host one."""
     if pg is None:
         return x
     import torch
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if pg.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     pg.all_reduce(t, op=pg.ReduceOp.MAX)
     return float(t.item())
 
