@@ -17,9 +17,15 @@ Algorithm 3):
 App. E (MaxCut, rounding): every column u of U gives the cut sgn(u) (0 counted as +1);
 the value of the sign vector z is <C, z z^T> = z^T C z in problem units, the MaxCut
 objective (1/4) z^T L z when C = L/4; the best of the r columns is kept.
+
+App. E (QAP, rounding): every column of U, its first entry dropped and the remaining nq^2
+reshaped into an nq x nq matrix (vec stacks columns), is projected onto the permutation
+matrices by the Hungarian method (a linear assignment maximising <M, Pi>); the permutation
+of least QAP cost tr(W Pi D Pi^T) over the columns is kept.
 """
 import numpy as np
 import scipy.linalg as sla
+import scipy.optimize as so
 import scipy.sparse as sp
 
 
@@ -82,3 +88,34 @@ def cut_weight(n, ei, ej, w, z):
     """Total weight of the edges whose ends z separates (each edge listed once)."""
     z = np.asarray(z)
     return float(np.sum(np.asarray(w)[z[np.asarray(ei)] != z[np.asarray(ej)]]))
+
+
+def qap_cost(W, D, Pi):
+    """tr(W Pi D Pi^T)."""
+    return float(np.trace(W @ Pi @ D @ Pi.T))
+
+
+def project_permutation(M):
+    """The permutation matrix Pi maximising <M, Pi> (Hungarian method)."""
+    nq = M.shape[0]
+    rows, cols = so.linear_sum_assignment(-np.asarray(M, dtype=np.float64))
+    Pi = np.zeros((nq, nq))
+    Pi[rows, cols] = 1.0
+    return Pi
+
+
+def qap_round(U, W, D):
+    """(least cost, its column, its permutation) over the columns of U ((nq^2 + 1) x r).
+    An eigenvector is defined up to sign; each column is oriented so that its first entry,
+    the one paired with X_00 = 1, is non-negative (for X = v v^T with v = [1; vec(B)] this
+    gives +vec(B)) before that entry is dropped."""
+    nq = W.shape[0]
+    best = (np.inf, -1, None)
+    for k in range(U.shape[1]):
+        sgn = 1.0 if U[0, k] >= 0.0 else -1.0
+        M = (sgn * U[1:, k]).reshape((nq, nq), order="F")
+        Pi = project_permutation(M)
+        c = qap_cost(W, D, Pi)
+        if c < best[0]:
+            best = (c, k, Pi)
+    return best

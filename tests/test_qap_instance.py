@@ -52,3 +52,33 @@ def test_oracle_dual_bound_covers_every_permutation():
     for _ in range(60):
         o.step()
         assert o.dual_bound() >= best - 1e-9 * abs(best)
+
+
+def test_qap_rounding_recovers_a_permutation_point():
+    """App. E rounding: with the sketch of X_Pi itself (a rank-one primal) the top column of
+    U is +-[1; vec(Pi)] / |.|, and the Hungarian projection returns Pi at its QAP cost."""
+    from oracle.nystrom import nystrom_reconstruct, qap_cost, qap_round
+    nq = 5
+    prob = I.qap_sdp(nq, 2)
+    W, D = prob.meta["W"], prob.meta["D"]
+    perm = (3, 0, 4, 1, 2)
+    Pi, X = _perm_point(nq, perm)
+    psi = np.random.default_rng(5).standard_normal((prob.n, nq))
+    U, lam = nystrom_reconstruct(X @ psi, psi)
+    cost, k, Pr = qap_round(U[:, :1], W, D)
+    np.testing.assert_array_equal(Pr, Pi)
+    assert cost == qap_cost(W, D, Pi)
+    assert abs(lam[0] - (1 + nq)) <= 1e-9 * (1 + nq)
+
+
+def test_qap_rounding_never_beats_the_optimum():
+    from oracle.nystrom import qap_round
+    nq = 5
+    prob = I.qap_sdp(nq, 1)
+    W, D = prob.meta["W"], prob.meta["D"]
+    opt = min(np.trace(W @ np.eye(nq)[list(p)] @ D @ np.eye(nq)[list(p)].T)
+              for p in itertools.permutations(range(nq)))
+    U = np.linalg.qr(np.random.default_rng(6).standard_normal((prob.n, 6)))[0]
+    cost, _, Pi = qap_round(U, W, D)
+    assert np.allclose(Pi.sum(0), 1) and np.allclose(Pi.sum(1), 1)
+    assert cost >= opt - 1e-9
