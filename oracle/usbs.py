@@ -134,6 +134,15 @@ def proj_N(sp_, u):
 
 # ---- state ----------------------------------------------------------------------------
 
+def split_past(S, k_p):
+    """eq. model_update_eigendecomposition: (Q_p, Q_c, L_c) with Q_p the eigenvectors of the
+    k_p largest eigenvalues of S (past information) and (Q_c, L_c) the remaining pairs."""
+    lam, Q = np.linalg.eigh(0.5 * (S + S.T))
+    order = np.argsort(-lam, kind="stable")
+    lam, Q = lam[order], Q[:, order]
+    return Q[:, :k_p], Q[:, k_p:], lam[k_p:]
+
+
 @dataclasses.dataclass
 class State:
     y: np.ndarray
@@ -274,12 +283,7 @@ class USBSOracle:
             st.cx, st.tr, st.ax = CX, trX, AX
             st.V = U
         else:
-            # eq. model_update_eigendecomposition: the k_p largest eigenpairs of S are the
-            # past part, the remaining k_c the current part
-            lam, Qs = np.linalg.eigh(0.5 * (S + S.T))
-            order = np.argsort(-lam, kind="stable")
-            lam, Qs = lam[order], Qs[:, order]
-            Qp, Qc, Lc = Qs[:, :self.k_p], Qs[:, self.k_p:], lam[self.k_p:]
+            Qp, Qc, Lc = split_past(S, self.k_p)
             Sc = (Qc * Lc) @ Qc.T
             # eq. x_bar_def through its implicit quantities (App. C)
             st.cx = eta * st.cx + float(np.sum(Vc * Sc))

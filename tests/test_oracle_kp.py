@@ -85,3 +85,17 @@ def test_k_p_zero_is_the_default_path():
     for _ in range(10):
         ia, ib = a.step(), b.step()
         assert ia["f_y"] == ib["f_y"] and ia["cx"] == ib["cx"]
+
+
+def test_planted_full_S_into_Xbar_is_caught(monkeypatch):
+    """If Xbar absorbed all of S (the k_p = 0 rule) while V still kept V Q_p, the
+    model-update invariants fail: Xbar_{t+1} must leave out V Q_p L_p Q_p^T V^T."""
+    real = U.split_past
+
+    def planted(S, k_p):
+        Qp, _, _ = real(S, k_p)
+        lam, Q = np.linalg.eigh(0.5 * (S + S.T))
+        return Qp, Q, lam
+    monkeypatch.setattr(U, "split_past", planted)
+    with pytest.raises(AssertionError):
+        test_model_update_invariants(1)

@@ -143,3 +143,16 @@ def test_fp32_sketch_uses_fp32_shift():
     nu64 = float(np.sqrt(n) * np.spacing(np.linalg.norm(Pd, 2)))
     B = Psi.astype(np.float64).T @ (Pd + nu64 * Psi.astype(np.float64))
     assert np.linalg.eigvalsh(0.5 * (B + B.T)).min() < 0.0
+
+
+def test_planted_transposed_factor_is_caught(monkeypatch):
+    """Solving E R^T = Y instead of E R = Y (a transposed Cholesky factor) breaks the exact
+    recovery of a low-rank matrix."""
+    import oracle.nystrom as NY
+    real = NY.sla.solve_triangular
+
+    def planted(a, b, trans=0, lower=False, **kw):
+        return real(a, b, trans=0 if trans == "T" else "T", lower=lower, **kw)
+    monkeypatch.setattr(NY.sla, "solve_triangular", planted)
+    with pytest.raises(AssertionError):
+        test_exact_for_rank_at_most_r(60, 3, 8)
