@@ -164,7 +164,7 @@ int usbs_destroy(usbs_ctx* ctx);
 int usbs_extreme_eigs(usbs_ctx* ctx, const double* y, int kc, double* evals,
                       double* evecs, usbs_eig_info* info);
 
-/* One iteration of Algorithm 1 (lines 4-11).  If the context has no iterate yet the
+/* One iteration of Algorithm 1 (the body of its loop).  If the context has no iterate yet the
  * cold start (y_0 = 0, Xbar_0 = 0, V_0 = top eigenvectors of C) is made first. */
 int usbs_step(usbs_ctx* ctx, usbs_step_info* info);
 

@@ -30,7 +30,7 @@ import scipy.sparse as sp
 
 
 def nystrom_shift(P):
-    """nu = sqrt(n) eps(||P||_2) of step 1, eps(x) the spacing of the sketch's own
+    """The shift nu = sqrt(n) eps(||P||_2), eps(x) the spacing of the sketch's own
     floating-point format at x: 2^(e - 24) for an FP32 sketch and 2^(e - 53) for an FP64
     one, x = f 2^e with f in [1/2, 1).  (The shift must cover the rounding of the stored
     sketch: with an FP32 sketch and the FP64 spacing, Psi^T (P + nu Psi) is indefinite.)"""
@@ -44,7 +44,7 @@ def nystrom_shift(P):
 
 
 def nystrom_reconstruct(P, Psi):
-    """Steps 1-5: (U, lam) with X_hat = U diag(lam) U^T, lam descending, U n x r.
+    """The reconstruction above: (U, lam) with X_hat = U diag(lam) U^T, lam descending, U n x r.
     The arithmetic is FP64 whatever the sketch's format; the shift follows the format."""
     nu = nystrom_shift(P)
     P = np.asarray(P, dtype=np.float64)

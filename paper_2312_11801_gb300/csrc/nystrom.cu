@@ -300,7 +300,7 @@ __device__ void ny_sort_desc(const double* A, int m, int* order) {
   __syncthreads();
 }
 
-// step 1: ||P||_2 from G0, nu, B = G1 + nu G2 (symmetrised), its Cholesky factor and R^-1
+// r x r core: ||P||_2 from G0, nu, B = G1 + nu G2 (symmetrised), its Cholesky factor and R^-1
 __global__ void __launch_bounds__(NY_T) k_ny_core(int64_t n, int r, const double* __restrict__ G, NyState* st) {
   __shared__ double A[NY_RMAX * NY_LD], V[NY_RMAX * NY_LD];
   __shared__ double Rm[NY_RMAX * NY_RMAX];
@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(NY_T) k_ny_core(int64_t n, int r, const double
   }
 }
 
-// step 2: E^T E = W Sigma^2 W^T; lam = max(sigma^2 - nu, 0) by descending sigma; M = W Sigma^-1
+// r x r decomposition: E^T E = W Sigma^2 W^T; lam = max(sigma^2 - nu, 0) by descending sigma; M = W Sigma^-1
 __global__ void __launch_bounds__(NY_T) k_ny_svd(int r, const double* __restrict__ G, NyState* st) {
   __shared__ double A[NY_RMAX * NY_LD], V[NY_RMAX * NY_LD];
   __shared__ int order[NY_RMAX];
