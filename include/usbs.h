@@ -47,8 +47,9 @@ extern "C" {
 #define USBS_ENUMERIC   -7   /* non-finite value in an FP64 reduction or the IPM */
 
 /* arithmetic of the bulk (n-sized) work; k-sized work is FP64 in both modes */
-#define USBS_PRECISION_FP64   0  /* SpMM, Lanczos basis, V, sketch in FP64 */
-#define USBS_PRECISION_MIXED  1  /* SpMM, reorthogonalisation, V, sketch in FP32 */
+#define USBS_PRECISION_FP64   0  /* SpMM, Lanczos basis and V in FP64 */
+#define USBS_PRECISION_MIXED  1  /* SpMM, reorthogonalisation and V in FP32 */
+/* The sketch P and its test matrix Psi are stored in FP32 in both modes (sums in FP64). */
 
 typedef struct usbs_ctx usbs_ctx;
 
