@@ -57,7 +57,7 @@ template <typename T>
 __device__ __forceinline__ void k_setup_diag_dev(const int cta, const int ncta, int n, const double* USBS_RESTRICT diagC, const int* USBS_RESTRICT dptr,
                              const int* USBS_RESTRICT dcon, const double* USBS_RESTRICT dval,
                              const double* USBS_RESTRICT y, T* USBS_RESTRICT dM) {
-  for (int i = cta * blockDim.x + threadIdx.x; i < n; i += ncta * blockDim.x) {
+  for (int64_t i = (int64_t)cta * blockDim.x + threadIdx.x; i < n; i += (int64_t)ncta * blockDim.x) {
     double s = diagC[i];
     for (int e = dptr[i]; e < dptr[i + 1]; ++e) s -= y[dcon[e]] * dval[e];
     dM[i] = (T)s;
@@ -81,7 +81,7 @@ __device__ __forceinline__ void k_spmm_dev(const int cta, const int ncta, int n,
                                               const int* USBS_RESTRICT col,
                                               const T* USBS_RESTRICT val, const T* USBS_RESTRICT d,
                                               const T* USBS_RESTRICT X, T* USBS_RESTRICT Y) {
-  for (int i = cta * blockDim.x + threadIdx.x; i < n; i += ncta * blockDim.x) {
+  for (int64_t i = (int64_t)cta * blockDim.x + threadIdx.x; i < n; i += (int64_t)ncta * blockDim.x) {
     T x[8], acc[8];
     load8(X + (size_t)8 * i, x);
     const T di = d[i];
@@ -154,9 +154,9 @@ __device__ __forceinline__ void k_gstats_dev(const int cta, const int ncta, int 
   double dacc[16];
 #pragma unroll
   for (int u = 0; u < 16; ++u) dacc[u] = 0.0;
-  for (int base = cta * GS_ROWS; base < m; base += ncta * GS_ROWS) {
+  for (int64_t base = (int64_t)cta * GS_ROWS; base < m; base += (int64_t)ncta * GS_ROWS) {
     if (tid < GS_ROWS) {
-      const int c = base + tid;
+      const int64_t c = base + tid;
       T* row = Gs + tid * AUG;
       if (c < m) {
         T g[KSV];
@@ -308,7 +308,7 @@ __device__ __forceinline__ void k_xupdate_dev(const int cta, const int ncta, int
   for (int u = 0; u < 39; ++u) acc[u] = 0.0;
   KahanSums<KSV> kg;
   kg.init();
-  for (int c = cta * blockDim.x + threadIdx.x; c < m; c += ncta * blockDim.x) {
+  for (int64_t c = (int64_t)cta * blockDim.x + threadIdx.x; c < m; c += (int64_t)ncta * blockDim.x) {
     T g[KSV];
     build_g<T>(c, con_ptr, ent_i, ent_j, ent_v, V, g);
     const double z = dot_svec<T>(g, ssv, ssf);
@@ -380,7 +380,7 @@ __device__ __forceinline__ void k_alt_dev(const int cta, const int ncta, int m, 
   for (int u = 0; u < 38; ++u) acc[u] = 0.0;
   KahanSums<KSV> kg;
   kg.init();
-  for (int c = cta * blockDim.x + threadIdx.x; c < m; c += ncta * blockDim.x) {
+  for (int64_t c = (int64_t)cta * blockDim.x + threadIdx.x; c < m; c += (int64_t)ncta * blockDim.x) {
     T g[KSV];
     build_g<T>(c, con_ptr, ent_i, ent_j, ent_v, V, g);
     const double z = dot_svec<T>(g, ssv, ssf);
@@ -422,7 +422,7 @@ __device__ __forceinline__ void k_constraint_eval_dev(const int cta, const int n
     for (int u = 0; u < KSV; ++u) ssf[u] = (float)ssv[u];
   }
   __syncthreads();
-  for (int c = cta * blockDim.x + threadIdx.x; c < m; c += ncta * blockDim.x) {
+  for (int64_t c = (int64_t)cta * blockDim.x + threadIdx.x; c < m; c += (int64_t)ncta * blockDim.x) {
     T g[KSV];
     build_g<T>(c, con_ptr, ent_i, ent_j, ent_v, V, g);
     z[c] = dot_svec<T>(g, ssv, ssf);
@@ -440,8 +440,8 @@ __device__ __forceinline__ void k_vt_psi_dev(const int cta, const int ncta, int 
   float acc[RMAX];
 #pragma unroll
   for (int s = 0; s < RMAX; ++s) acc[s] = 0.f;
-  for (int base = (cta * 8 + warp) * 4; base < n; base += ncta * 32) {
-    const int i = base + rr;
+  for (int64_t base = ((int64_t)cta * 8 + warp) * 4; base < n; base += (int64_t)ncta * 32) {
+    const int64_t i = base + rr;
     if (i < n) {
       const float v = (float)V[(size_t)8 * i + a];
       const float* pr = Psi + (size_t)r * i;

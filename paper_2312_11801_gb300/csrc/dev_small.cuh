@@ -1332,7 +1332,7 @@ __device__ __forceinline__ void k_begin_step_dev(DevScalars* sc) {
 __device__ __forceinline__ void k_commit_dev(const int cta, const int ncta, int m, const DevScalars* USBS_RESTRICT sc, const double* USBS_RESTRICT ycand,
                          double* USBS_RESTRICT y) {
   if (!sc->descent) return;
-  for (int c = cta * blockDim.x + threadIdx.x; c < m; c += ncta * blockDim.x) y[c] = ycand[c];
+  for (int64_t c = (int64_t)cta * blockDim.x + threadIdx.x; c < m; c += (int64_t)ncta * blockDim.x) y[c] = ycand[c];
 }
 
 __device__ __forceinline__ void k_lanczos_reset_dev(DevLanczos* lz) {

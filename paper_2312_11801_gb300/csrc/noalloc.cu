@@ -29,8 +29,8 @@ __global__ void __launch_bounds__(256) k_na_vt_psi(int n, int r, const float* __
   float acc[NA_RMAX];
 #pragma unroll
   for (int s = 0; s < NA_RMAX; ++s) acc[s] = 0.f;
-  for (int base = (blockIdx.x * 8 + warp) * 4; base < n; base += gridDim.x * 32) {
-    const int i = base + rr;
+  for (int64_t base = ((int64_t)blockIdx.x * 8 + warp) * 4; base < n; base += (int64_t)gridDim.x * 32) {
+    const int64_t i = base + rr;
     if (i < n) {
       const float v = V[(size_t)8 * i + a];
       const float* pr = Psi + (size_t)r * i;
@@ -93,11 +93,13 @@ __global__ void __launch_bounds__(256) k_na_sketch(int n, int r, const float* __
   }
 }
 
-// Device address of g_na_scratch, looked up once per device with that device current.
+// Device address of g_na_scratch and the SM count, looked up once per device with that
+// device current.
 std::mutex g_na_mutex;
 double* g_na_ptr[NA_MAX_DEVICES] = {};
+int g_na_sms[NA_MAX_DEVICES] = {};
 
-int scratch_address(double** out) {
+int scratch_address(double** out, int* sms) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) {
     cudaGetLastError();
@@ -110,9 +112,16 @@ int scratch_address(double** out) {
       cudaGetLastError();
       return USBS_ECUDA;
     }
+    int nsm = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) {
+      cudaGetLastError();
+      return USBS_ECUDA;
+    }
+    g_na_sms[dev] = nsm;
     g_na_ptr[dev] = static_cast<double*>(p);
   }
   *out = g_na_ptr[dev];
+  *sms = g_na_sms[dev];
   return USBS_OK;
 }
 
@@ -127,7 +136,8 @@ extern "C" int usbs_sketch_update_static(int64_t n, int r, const float* V_dev,
       !P_dev)
     return USBS_EINVAL;
   double* scratch = nullptr;
-  const int rc = scratch_address(&scratch);
+  int sms = 0;
+  const int rc = scratch_address(&scratch, &sms);
   if (rc != USBS_OK) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   double* partials = scratch;
@@ -135,7 +145,7 @@ extern "C" int usbs_sketch_update_static(int64_t n, int r, const float* V_dev,
   k_na_vt_psi<<<NA_PARTS, 256, 0, st>>>((int)n, r, V_dev, Psi_dev, partials);
   k_na_reduce<<<1, 256, 0, st>>>(partials, NA_PARTS, 8 * r, B);
   int64_t g = (n * r + 255) / 256;
-  if (g > 152 * 8) g = 152 * 8;
+  if (g > (int64_t)sms * 8) g = (int64_t)sms * 8;   // eight 256-thread CTAs per SM
   k_na_sketch<<<(int)g, 256, 0, st>>>((int)n, r, V_dev, S_dev, B, P_dev, (float)eta);
   if (cudaGetLastError() != cudaSuccess) return USBS_ECUDA;
   return USBS_OK;

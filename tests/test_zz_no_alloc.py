@@ -41,6 +41,10 @@ def test_static_sketch_update_matches_context_entry_point():
         stream.synchronize()
         got, ref = P_static.double().cpu().numpy(), P_ctx.double().cpu().numpy()
         assert rel_err(got, ref) <= 2e-5, (call, rel_err(got, ref))
+        # and the update itself, from its definition with the FP32-rounded V
+        Vr = Vd.double().cpu().numpy()
+        dense = eta * P0.astype(np.float64) + Vr @ (S @ (Vr.T @ psi.astype(np.float64)))
+        assert rel_err(got, dense) <= 2e-5, (call, rel_err(got, dense))
 
 
 def test_static_sketch_update_rejects_oversized_rank():
