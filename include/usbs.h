@@ -34,7 +34,8 @@
 extern "C" {
 #endif
 
-#define USBS_ABI_VERSION 2   /* 2: usbs_eig_info.reruns, usbs_nystrom_round */
+#define USBS_ABI_VERSION 3   /* 2: usbs_eig_info.reruns, usbs_nystrom_round;
+                                3: certification of f(y) and the objective-relative gate */
 
 /* status codes */
 #define USBS_OK          0
@@ -73,6 +74,19 @@ typedef struct usbs_params {
   uint64_t seed;           /* seeds the random start/deflation vectors of Lanczos */
   void*  stream;           /* cudaStream_t to run on; NULL = own stream */
   int    device;           /* CUDA device ordinal; -1 = current device */
+  /* Certification of the dual value (usbs_solve).  f(y) = alpha lambda_max(C - A*(y))_+
+   * + <b, y> bounds the optimum from above only through the exact lambda_max (eq.
+   * objective_subopt_upper_bound), and a Ritz value of a budgeted eigen solve is a lower
+   * estimate of it.  With certify_restarts > 0, once both gates pass, usbs_solve first
+   * recomputes f at the centre y by an eigen solve with a 64-column basis (at most n - 16),
+   * at most certify_restarts cycles and residual tolerance certify_tol, keeps the larger of
+   * the two values of f(y), and re-evaluates the gates with it; the solve goes on if they
+   * no longer pass.  0 = off (the default). */
+  int    certify_restarts;
+  double certify_tol;      /* 0 = 1e-7 (MIXED) or 1e-10 (FP64) */
+  /* When > 0, convergence also needs |f(y) - <C,X>| / |<C,X>| <= obj_gap_tol: the gap
+   * relative to the objective itself, beside the paper's 1 + |<C,X>| denominator. */
+  double obj_gap_tol;
 } usbs_params;
 
 typedef struct usbs_eig_info {
@@ -108,10 +122,14 @@ typedef struct usbs_step_info {
 
 typedef struct usbs_result {
   int    iters;            /* iterations run by this call */
-  int    converged;        /* both gates <= tol */
+  int    converged;        /* both gates <= tol (and the objective-relative gap, if asked) */
   int    descent_steps;
-  long long matvecs;       /* total Lanczos single-vector products */
-  usbs_step_info last;     /* diagnostics of the last iteration */
+  long long matvecs;       /* total Lanczos single-vector products (certification included) */
+  usbs_step_info last;     /* diagnostics of the last iteration (f_y, relgap and dual_bound
+                              after certification when it ran) */
+  int    certifications;   /* certifying eigen solves run (usbs_params.certify_restarts) */
+  double cert_residual;    /* max top-k_c Ritz residual of the last one (scaled units) */
+  double obj_gap;          /* |f(y) - <C,X>| / |<C,X>| of the last iterate */
 } usbs_result;
 
 /* Fill *p with the defaults listed above. */
@@ -172,7 +190,10 @@ int usbs_step(usbs_ctx* ctx, usbs_step_info* info);
 /*
  * usbs_solve -- iterate until relgap <= tol and relinf <= tol (App. E gates, scaled
  * units) or max_iters.  warm_start = 0 restarts from the cold start; 1 continues from
- * the current state (after usbs_set_state, usbs_grow or earlier steps).
+ * the current state (after usbs_set_state, usbs_grow or earlier steps).  With
+ * usbs_params.certify_restarts > 0 the gates are accepted only after f(y) has been
+ * recomputed by a certifying eigen solve (see usbs_params); with obj_gap_tol > 0 the
+ * objective-relative gap must pass too.
  * Returns USBS_OK when converged, USBS_ENOTCONV at the cap (out is filled either way).
  */
 int usbs_solve(usbs_ctx* ctx, int warm_start, double tol, usbs_result* out);

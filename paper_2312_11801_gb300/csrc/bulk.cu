@@ -110,6 +110,23 @@ __global__ void __launch_bounds__(256) k_reduce(const double* __restrict__ parti
   k_reduce_dev(blockIdx.x, gridDim.x, partials, nparts, nvals, out, mask);
 }
 
+// per-CTA partial sums of <a, b> (m FP64 entries), fixed order within the CTA
+__global__ void __launch_bounds__(256) k_dot(int64_t m, const double* __restrict__ a,
+                                             const double* __restrict__ b, double* __restrict__ partials) {
+  __shared__ double ws[8];
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+    s = fma(a[i], b[i], s);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += ws[w];
+    partials[(size_t)blockIdx.x * PART_STRIDE] = t;
+  }
+}
+
 __global__ void k_reduce_max(const double* __restrict__ partials, int nparts, int slot,
                              double* __restrict__ out) {
   k_reduce_max_dev(blockIdx.x, gridDim.x, partials, nparts, slot, out);
@@ -128,6 +145,15 @@ int red_grid(Ctx* c, int64_t rows, int rows_per_cta) {
 void reduce_partials(Ctx* c, int nparts, int nvals, double* out, const int* mask) {
   USBS_LAUNCH_B(c, USBS_KIND_REDUCE, mask ? 0.0 : 8.0 * nvals * (nparts + 1));
   k_reduce<<<(nvals + 31) / 32, 256, 0, c->stream>>>(c->partials, nparts, nvals, out, mask);
+}
+
+void launch_dot(Ctx* c, const double* a, const double* b, int64_t m, double* out) {
+  const int g = red_grid(c, m, 256);
+  {
+    USBS_LAUNCH_B(c, USBS_KIND_REDUCE, 16.0 * m);
+    k_dot<<<g, 256, 0, c->stream>>>(m, a, b, c->partials);
+  }
+  reduce_partials(c, g, 1, out);
 }
 
 // algorithmic bytes of a per-constraint kernel: each entry (i, j, value) and con_ptr once,

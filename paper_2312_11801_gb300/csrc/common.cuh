@@ -55,6 +55,8 @@ struct DevScalars {
   double B_sketch[KB * RMAX];  // V^T Psi (k x r)
   int descent, ipm_iters, has_eta, status;
   int t, n_alt, matvecs, pad;
+  // certification of f(y) at the centre (usbs_solve with certify_restarts > 0)
+  double f_cert, lam_cert;
 };
 
 // ---- Lanczos device state -------------------------------------------------------------
@@ -223,7 +225,8 @@ constexpr int RED_AUG = 1152;     // AUG x AUG (full)
 constexpr int RED_VEC = 2816;     // 36 + scalars (alternation / candidate)
 constexpr int RED_SK = 2944;      // 8 x 32 sketch B
 constexpr int RED_VC = 3200;      // 64, V^T C V
-constexpr int RED_TOTAL = 3328;
+constexpr int RED_CERT = 3328;    // 8: <b, y> of the certification
+constexpr int RED_TOTAL = 3336;
 constexpr int PART_STRIDE = 1024; // doubles per CTA in partials
 
 // ---- error helpers ---------------------------------------------------------------------
@@ -289,6 +292,11 @@ void launch_commit(Ctx* c);
 void launch_cold(Ctx* c);
 void launch_begin_step(Ctx* c);
 void launch_lanczos_reset(Ctx* c);
+// f(y) at the centre from the certifying eigen solve's top Ritz value and <b, y> (in
+// red + RED_CERT); keeps the larger value of f(y) and re-evaluates the gap
+void launch_certify(Ctx* c);
+// out = <a, b> over m FP64 entries (per-CTA partials reduced in a fixed order)
+void launch_dot(Ctx* c, const double* a, const double* b, int64_t m, double* out);
 
 // device address of a member of a device-resident struct (no dereference on the host)
 #define DEV_FIELD(base, Type, field, Elem) \

@@ -1312,6 +1312,21 @@ __device__ __forceinline__ void k_finish_dev(DevScalars* sc, const DevLanczos* l
   if (!isfinite(sc->f_y) || !isfinite(cx_new)) sc->status = USBS_ENUMERIC;
 }
 
+// f(y) at the centre y_t from a longer eigen solve (usbs_solve's certification).  A Ritz
+// value never exceeds lambda_max, so of two evaluations of f(y_t) the larger is the more
+// accurate; it replaces f(y_t) for the gates and for the next descent tests.
+__device__ __forceinline__ void k_certify_dev(DevScalars* sc, const DevLanczos* lz, const double* USBS_RESTRICT red,
+                                              double alpha) {
+  if (threadIdx.x != 0) return;
+  const double lam = lz->theta[0];
+  const double f = alpha * fmax(lam, 0.0) + red[RED_CERT];
+  sc->f_cert = f;
+  sc->lam_cert = lam;
+  if (f > sc->f_y) sc->f_y = f;
+  sc->relgap = fabs(sc->f_y - sc->cx) / (1.0 + fabs(sc->cx));
+  if (!isfinite(sc->f_y)) sc->status = USBS_ENUMERIC;
+}
+
 __device__ __forceinline__ void k_cold_dev(DevScalars* sc, const DevLanczos* lz, double alpha) {
   if (threadIdx.x != 0) return;
   sc->f_y = alpha * fmax(lz->theta[0], 0.0);

@@ -408,6 +408,9 @@ static void fill_defaults(usbs_params* p) {
   p->seed = 0;
   p->stream = nullptr;
   p->device = -1;
+  p->certify_restarts = 0;
+  p->certify_tol = 0.0;   // 0 = by precision
+  p->obj_gap_tol = 0.0;
 }
 
 static int init_ctx(Ctx* c, int64_t n, int64_t m, int64_t nnzA, const usbs_params* p,
@@ -431,6 +434,11 @@ static int init_ctx(Ctx* c, int64_t n, int64_t m, int64_t nnzA, const usbs_param
   c->fp64 = q.precision == USBS_PRECISION_FP64;
   c->alpha = q.alpha > 0.0 ? q.alpha : 2.0;
   if (!(q.lanczos_tol > 0.0)) q.lanczos_tol = c->fp64 ? 1e-10 : 1e-6;
+  if (q.certify_restarts < 0 || q.obj_gap_tol < 0.0) {
+    c->err = "certify_restarts and obj_gap_tol must be >= 0";
+    return USBS_EINVAL;
+  }
+  if (!(q.certify_tol > 0.0)) q.certify_tol = c->fp64 ? 1e-10 : 1e-7;
   if (q.lanczos_restarts < 1) q.lanczos_restarts = 10;
   if (q.ipm_max_iter < 1) q.ipm_max_iter = 100;
   if (q.max_alt < 1) q.max_alt = 50;
@@ -720,6 +728,52 @@ static int step_dispatch(Ctx* c, usbs_step_info* info) {
   return c->fp64 ? step_impl<double>(c, info) : step_impl<float>(c, info);
 }
 
+// Certification of f at the centre y_t: an eigen solve with a 64-column basis (at most
+// n - 16), certify_restarts cycles and tolerance certify_tol, started from V; then
+// f = alpha lambda_+ + <b, y_t> on the device, the larger of the two values of f(y_t)
+// kept and the relative gap re-evaluated (k_certify).  V is left unchanged.
+template <typename T>
+static int certify_impl(Ctx* c, double* residual, int* matvecs) {
+  const int J0 = c->J, keep0 = c->keep, R0 = c->prm.lanczos_restarts;
+  const double tol0 = c->prm.lanczos_tol;
+  int J = (int)std::min<int64_t>(JMAX, 16 * ((c->n - 16) / 16));
+  if (J == 48) J = 32;
+  c->J = J;
+  c->keep = J / 2;
+  c->prm.lanczos_restarts = c->prm.certify_restarts;
+  c->prm.lanczos_tol = c->prm.certify_tol;
+  LanczosOut lo;
+  const int rc = lanczos<T>(c, c->y, c->V, c->Vnew, &lo);
+  c->J = J0;
+  c->keep = keep0;
+  c->prm.lanczos_restarts = R0;
+  c->prm.lanczos_tol = tol0;
+  USBS_TRY(rc);
+  launch_dot(c, c->b, c->y, c->m, c->red + RED_CERT);
+  launch_certify(c);
+  USBS_TRY(check_launch(c, "certification"));
+  USBS_CUDA_TRY(c, cudaMemcpyAsync(c->h_sc, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost,
+                                   c->stream));
+  USBS_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  *residual = lo.max_res;
+  *matvecs = lo.matvecs;
+  if (c->h_sc->status != 0) {
+    c->err = "non-finite value in the certification of f(y)";
+    return USBS_ENUMERIC;
+  }
+  return USBS_OK;
+}
+
+// gap relative to the objective itself (scaled units; the ratio is unit-free)
+static double obj_gap_of(double f, double cx) {
+  return std::fabs(f - cx) / std::max(std::fabs(cx), 1e-300);
+}
+
+static bool gates_pass(const Ctx* c, const usbs_step_info& info, double tol) {
+  if (!(info.relgap <= tol && info.relinf <= tol)) return false;
+  return !(c->prm.obj_gap_tol > 0.0) || obj_gap_of(info.f_y, info.cx) <= c->prm.obj_gap_tol;
+}
+
 }  // namespace usbs
 
 // =======================================================================================
@@ -847,11 +901,24 @@ int usbs_solve(usbs_ctx* ctx, int warm_start, double tol, usbs_result* out) {
     res.iters++;
     res.descent_steps += info.descent;
     res.last = info;
-    if (info.relgap <= tol && info.relinf <= tol) {
-      res.converged = 1;
-      break;
+    if (!gates_pass(c, info, tol)) continue;
+    if (c->prm.certify_restarts > 0) {
+      double resid = 0.0;
+      int mv = 0;
+      rc = c->fp64 ? certify_impl<double>(c, &resid, &mv) : certify_impl<float>(c, &resid, &mv);
+      if (rc != USBS_OK) break;
+      res.certifications++;
+      res.cert_residual = resid;
+      info.f_y = c->h_sc->f_y;
+      info.relgap = c->h_sc->relgap;
+      info.dual_bound = c->h_sc->f_y * c->c_scale * c->tau;
+      res.last = info;
+      if (!gates_pass(c, info, tol)) continue;
     }
+    res.converged = 1;
+    break;
   }
+  res.obj_gap = obj_gap_of(res.last.f_y, res.last.cx);
   res.matvecs = c->total_matvecs - mv0;
   if (out) *out = res;
   if (rc != USBS_OK) return rc;
@@ -874,6 +941,7 @@ int batch_result(Ctx* c, usbs_result* out) {
   if (c->batch_iters > 0) {
     c->h_sc->n_alt = c->batch_n_alt;
     fill_info(c, *c->h_sc, c->batch_last_matvecs, &res.last);
+    res.obj_gap = obj_gap_of(res.last.f_y, res.last.cx);
   }
   if (out) *out = res;
   if (c->batch_status != USBS_OK) {

@@ -46,6 +46,11 @@ __global__ void k_finish(DevScalars* sc, const DevLanczos* lz, const double* __r
   k_finish_dev(sc, lz, red, kc, alpha, beta, bnorm);
 }
 
+__global__ void k_certify(DevScalars* sc, const DevLanczos* lz, const double* __restrict__ red,
+                          double alpha) {
+  k_certify_dev(sc, lz, red, alpha);
+}
+
 __global__ void k_cold(DevScalars* sc, const DevLanczos* lz, double alpha) {
   k_cold_dev(sc, lz, alpha);
 }
@@ -126,6 +131,9 @@ void launch_finish(Ctx* c) {
   USBS_LAUNCH(c, USBS_KIND_SMALL);
   k_finish<<<1, 32, 0, c->stream>>>(c->sc, c->lz, c->red, c->kc, c->alpha, c->prm.beta, c->bnorm);
 }
+
+void launch_certify(Ctx* c) {
+  USBS_LAUNCH(c, USBS_KIND_SMALL); k_certify<<<1, 32, 0, c->stream>>>(c->sc, c->lz, c->red, c->alpha); }
 
 void launch_cold(Ctx* c) {
   USBS_LAUNCH(c, USBS_KIND_SMALL); k_cold<<<1, 32, 0, c->stream>>>(c->sc, c->lz, c->alpha); }

@@ -28,7 +28,7 @@ import numpy as np
 __all__ = [
     "Problem", "laplacian_maxcut", "maxcut_er", "maxcut_torus", "maxcut_rgg",
     "grow_rgg", "clustering_sdp", "maxcut_from_edges", "complete_graph_edges",
-    "cycle_edges", "batched_er", "qap_sdp", "gaussian_psi", "save_npz", "load_npz",
+    "cycle_edges", "batched_er", "qap_sdp", "dual_sample", "gaussian_psi", "save_npz", "load_npz",
 ]
 
 
@@ -343,6 +343,14 @@ def batched_er(count=512, n_lo=100, n_hi=4000, avg_deg=8.0, seed0=0):
     ns = rng.integers(n_lo, n_hi + 1, size=count)
     return [maxcut_er(int(nn), avg_deg, seed=seed0 + s, weights="uniform")
             for s, nn in enumerate(ns)]
+
+
+def dual_sample(prob: Problem, seed=11, scale=0.05):
+    """A seeded dual point for eigen-solve tests, in the scaled units of App. E: i.i.d.
+    |N(0, 1)| * scale / sqrt(n) per constraint (non-negative, so every inequality row
+    is admissible)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.abs(rng.standard_normal(prob.m)) * scale / math.sqrt(prob.n)
 
 
 def gaussian_psi(n, r, seed=1, dtype=np.float32):

@@ -29,7 +29,9 @@ class usbs_params(ctypes.Structure):
                 ("ipm_mu_tol", ctypes.c_double), ("ipm_max_iter", ctypes.c_int),
                 ("max_alt", ctypes.c_int), ("alt_tol", ctypes.c_double),
                 ("trace_hint", ctypes.c_double), ("max_iters", ctypes.c_int),
-                ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p), ("device", ctypes.c_int)]
+                ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p), ("device", ctypes.c_int),
+                ("certify_restarts", ctypes.c_int), ("certify_tol", ctypes.c_double),
+                ("obj_gap_tol", ctypes.c_double)]
 
 
 class usbs_eig_info(ctypes.Structure):
@@ -51,7 +53,8 @@ class usbs_step_info(ctypes.Structure):
 class usbs_result(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int),
                 ("descent_steps", ctypes.c_int), ("matvecs", ctypes.c_longlong),
-                ("last", usbs_step_info)]
+                ("last", usbs_step_info), ("certifications", ctypes.c_int),
+                ("cert_residual", ctypes.c_double), ("obj_gap", ctypes.c_double)]
 
 
 class usbs_server_params(ctypes.Structure):

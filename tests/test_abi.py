@@ -46,7 +46,8 @@ def test_param_defaults_and_version(U):
     p = U.params_default()
     assert p.rho == 0.01 and p.beta == 0.25 and p.k_c == 8 and p.k_p == 0
     assert p.lanczos_restarts == 10 and p.ipm_mu_tol == 1e-7 and p.max_alt == 50
-    assert U.load().usbs_abi_version() == 2
+    assert p.certify_restarts == 0 and p.obj_gap_tol == 0.0
+    assert U.load().usbs_abi_version() == 3
 
 
 def _expect_einval(U, prob, match, **kw):
@@ -60,6 +61,7 @@ def test_invalid_arguments_rejected_on_the_host(U):
     p = I.maxcut_er(40, 4, seed=1)
     _expect_einval(U, p, "k_p", k_p=1)
     _expect_einval(U, p, "k_c", k_c=9)
+    _expect_einval(U, p, "certify_restarts", certify_restarts=-1)
     _expect_einval(U, p, "Psi", r=4)
     small = I.maxcut_er(28, 4, seed=1)
     _expect_einval(U, small, "n >= 32")
