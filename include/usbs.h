@@ -59,7 +59,10 @@ typedef struct usbs_params {
   double rho;              /* proximal parameter (eq. proposal_step); default 0.01 */
   double beta;             /* descent fraction (eq. descent_cond); default 0.25 */
   int    k_c;              /* current eigenvectors kept in V, 1..8; default 8 */
-  int    k_p;              /* past-information columns; only 0 is supported */
+  int    k_p;              /* past-information columns (Sec. 3, eqs. model_update_
+                              eigendecomposition, x_bar_def, v_next_def): V holds
+                              k_c + k_p <= 8 columns; the k_p leading eigenvectors of S stay
+                              in V and leave Xbar.  Default 0 (Xbar = X) */
   int    r;                /* sketch rank (Sec. 4); 0 = no sketch */
   int    precision;        /* USBS_PRECISION_*; default MIXED */
   int    lanczos_basis;    /* block Lanczos basis columns J: 16, 32 or 64 (at most n - 16) */
@@ -155,7 +158,7 @@ const char* usbs_last_error(const usbs_ctx* ctx);
  *  b        : m FP64.  is_ineq : m uint8, nonzero = row is <A_c, X> <= b_c.
  *  Psi      : n x r FP32 row-major sketch test matrix (Sec. 4), required iff p->r > 0.
  *  p        : parameters (NULL = defaults).
- * Errors: USBS_EINVAL (sizes, index ranges, r > 0 without Psi, n < 32, k_p != 0,
+ * Errors: USBS_EINVAL (sizes, index ranges, r > 0 without Psi, n < 32, k_c + k_p > 8,
  * unknown trace), USBS_ENOMEM, USBS_ECUDA.  *out is NULL on failure.
  */
 int usbs_create(usbs_ctx** out, int64_t n, const int64_t* C_rowptr, const int32_t* C_col,
@@ -233,7 +236,7 @@ int usbs_get_primal_constraints(usbs_ctx* ctx, double* ax);
 /*
  * Complete iterate state (USBS has no iteration-dependent parameters, Sec. 3, so this
  * is a checkpoint and the warm-start input).  Layout of the FP64 host buffer, problem
- * units: [y (m), A Xbar (m), <C,Xbar>, tr Xbar, f(y), V (n*k_c row-major), P (n*r)].
+ * units: [y (m), A Xbar (m), <C,Xbar>, tr Xbar, f(y), V (n*(k_c+k_p) row-major), P (n*r)].
  * usbs_state_size gives its length in doubles.
  */
 int64_t usbs_state_size(const usbs_ctx* ctx);

@@ -16,7 +16,10 @@ int batch_launch_f64_j32(const std::vector<Ctx*>& cs, cudaStream_t st, double to
 // both precisions, J = 64 in mixed precision) and no per-step host work (debug checks,
 // event profiling).
 bool batch_eligible(const Ctx* c) {
-  if (c->debug || c->prof) return false;
+  // the per-step path alone carries past information, certification and the
+  // objective-relative gate
+  if (c->debug || c->prof || c->kp > 0 || c->prm.certify_restarts > 0 || c->prm.obj_gap_tol > 0.0)
+    return false;
   if (c->fp64) return c->J == 32;
   return c->J == 32 || c->J == 64;
 }

@@ -110,6 +110,21 @@ __global__ void __launch_bounds__(256) k_reduce(const double* __restrict__ parti
   k_reduce_dev(blockIdx.x, gridDim.x, partials, nparts, nvals, out, mask);
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) k_constraint_axpy(int m, const int* __restrict__ con_ptr,
+                                                         const int* __restrict__ ent_i, const int* __restrict__ ent_j,
+                                                         const T* __restrict__ ent_v, const T* __restrict__ V,
+                                                         const double* __restrict__ S, const double* __restrict__ eta,
+                                                         const double* __restrict__ ax, double* __restrict__ out) {
+  k_constraint_axpy_dev<T>(blockIdx.x, gridDim.x, m, con_ptr, ent_i, ent_j, ent_v, V, S, eta, ax, out);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_vnext(int n, const T* __restrict__ V, const double* __restrict__ Qp,
+                                               const T* __restrict__ U, int kp, int kc, T* __restrict__ W) {
+  k_vnext_dev<T>(blockIdx.x, gridDim.x, n, V, Qp, U, kp, kc, W);
+}
+
 // per-CTA partial sums of <a, b> (m FP64 entries), fixed order within the CTA
 __global__ void __launch_bounds__(256) k_dot(int64_t m, const double* __restrict__ a,
                                              const double* __restrict__ b, double* __restrict__ partials) {
@@ -245,6 +260,21 @@ void Bulk<T>::constraint_eval(Ctx* c, const void* V, const double* S, double* z)
   USBS_LAUNCH_B(c, USBS_KIND_CONSTR, constr_bytes(c, sizeof(T), 8.0));
   k_constraint_eval<T><<<row_grid(c, c->m), 256, 0, c->stream>>>(
       (int)c->m, c->con_ptr, c->ent_i, c->ent_j, (const T*)c->ent_v, (const T*)V, S, z);
+}
+
+template <typename T>
+void Bulk<T>::constraint_axpy(Ctx* c, const void* V, const double* S, const double* eta_dev,
+                              const double* ax, double* out) {
+  USBS_LAUNCH_B(c, USBS_KIND_CONSTR, constr_bytes(c, sizeof(T), 16.0));
+  k_constraint_axpy<T><<<row_grid(c, c->m), 256, 0, c->stream>>>(
+      (int)c->m, c->con_ptr, c->ent_i, c->ent_j, (const T*)c->ent_v, (const T*)V, S, eta_dev, ax, out);
+}
+
+template <typename T>
+void Bulk<T>::vnext(Ctx* c, const void* V, const double* Qp, const void* U, void* W) {
+  USBS_LAUNCH_B(c, USBS_KIND_RESTART, 24.0 * sizeof(T) * c->n);
+  k_vnext<T><<<row_grid(c, c->n), 256, 0, c->stream>>>((int)c->n, (const T*)V, Qp, (const T*)U, c->kp,
+                                                        c->kc, (T*)W);
 }
 
 void reduce_max_slot(Ctx* c, int nparts, int slot, double* out) {

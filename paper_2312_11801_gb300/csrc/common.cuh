@@ -1,6 +1,7 @@
 // Internal declarations shared by the libusbs translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -57,6 +58,12 @@ struct DevScalars {
   int t, n_alt, matvecs, pad;
   // certification of f(y) at the centre (usbs_solve with certify_restarts > 0)
   double f_cert, lam_cert;
+  // the primal iterate X_{t+1} = eta Xbar_t + V S V^T (gates, objective); cx and tr above
+  // hold Xbar's, which differ from these when k_p > 0
+  double cx_it, tr_it;
+  double cx_prev, tr_prev;   // Xbar_t's <C, Xbar>, tr Xbar before the step's update
+  // past information (k_p > 0): S = S_p + S_c and the k_p leading eigenvectors Q_p of S
+  double Sp[64], Sc[64], Qp[64];
 };
 
 // ---- Lanczos device state -------------------------------------------------------------
@@ -82,6 +89,13 @@ struct DevLanczos {
                                // its Rayleigh-Ritz step was skipped, the host reruns it
 };
 
+// TMA tensor map of one n x 8 FP32 buffer of a context (tc_orth.cu)
+struct TmaEntry {
+  const char* base;
+  size_t bytes;
+  CUtensorMap map;
+};
+
 template <typename T>
 struct Buf {
   T* p = nullptr;
@@ -94,6 +108,9 @@ struct Ctx {
   int nnz_off = 0;              // off-diagonal entries of the merged operator pattern
   usbs_params prm{};
   int kc = 8, r = 0, J = 64, keep = 32;
+  int kp = 0;                   // past-information columns (Sec. 3); V holds kdim = kc + kp
+  int kdim = 8;
+  int kconv = 8;                // top Ritz pairs whose residuals end an eigen solve
   bool fp64 = false;
   bool has_offdiag_A = false;
   bool any_ineq = false;
@@ -108,6 +125,8 @@ struct Ctx {
   bool speculate = true;        // run Lanczos cycles without the masked passes, rerun a cycle
                                 // that needed them (USBS_NO_SPECULATE=1 turns this off)
   long long total_matvecs = 0;
+  bool use_tc = false;          // FP32 Gram-Schmidt and restart tiles on tcgen05 (USBS_TCGEN05=1)
+  std::vector<TmaEntry> tma;    // tensor maps of the FP32 n x 8 buffers
 
   // operator (scaled): merged off-diagonal CSR pattern + diagonal
   int* rowptr = nullptr;        // n+1
@@ -258,6 +277,11 @@ template <typename T> struct Bulk {
   static void sketch_update(Ctx* c, const void* V, const double* S, const double* Bsk, float* P,
                             const float* Psi, const double* eta_dev, double eta_host);
   static void constraint_eval(Ctx* c, const void* V, const double* S, double* z);
+  // out = eta ax + A(V S V^T), eta on the device (Xbar's constraint values when k_p > 0)
+  static void constraint_axpy(Ctx* c, const void* V, const double* S, const double* eta_dev,
+                              const double* ax, double* out);
+  // W = [V Q_p | U_{:, :k_c} | 0] (the block whose QR is V_{t+1} when k_p > 0)
+  static void vnext(Ctx* c, const void* V, const double* Qp, const void* U, void* W);
 };
 
 // shared-memory-staged block Gram-Schmidt kernels (orth.cu); grid = orth_grid(c, n)
@@ -275,6 +299,15 @@ template <typename T> struct Orth {
 // CTAs of a tiled Gram-Schmidt launch: one per tile of rows, at most what stays resident
 // on every SM at once for that kernel and shared-memory size, at most max_parts
 int orth_grid(Ctx* c, int64_t rows, const void* kernel, size_t smem);
+// tcgen05 tiles of the mixed-precision path (tc_orth.cu).  tc_proj / tc_update return the
+// grid they launched (0: no tensor map for a buffer, nothing launched); tc_final /
+// tc_restart return whether they launched.
+void tc_register(Ctx* c);
+int tc_proj(Ctx* c, const void* Q, int nb, const void* W, const int* mask);
+int tc_update(Ctx* c, const void* Q, int nb, void* W, const int* mask);
+bool tc_final(Ctx* c, const void* Q, int nb, const void* W, void* out, const int* mask, uint64_t seed);
+bool tc_restart(Ctx* c, const void* Q, int J, int nout, const double* Y, void* out, const void* resid,
+                int resid_slot);
 // rows of partials a context needs: ceil(max(n, m) / 64) + 1, at most RED_GRID_MAX
 int64_t parts_needed(int64_t n, int64_t m);
 
@@ -295,6 +328,8 @@ void launch_lanczos_reset(Ctx* c);
 // f(y) at the centre from the certifying eigen solve's top Ritz value and <b, y> (in
 // red + RED_CERT); keeps the larger value of f(y) and re-evaluates the gap
 void launch_certify(Ctx* c);
+// S = S_p + S_c split of the k_p largest eigenpairs and Xbar's scalars (k_p > 0)
+void launch_kp_split(Ctx* c);
 // out = <a, b> over m FP64 entries (per-CTA partials reduced in a fixed order)
 void launch_dot(Ctx* c, const double* a, const double* b, int64_t m, double* out);
 

@@ -429,6 +429,61 @@ __device__ __forceinline__ void k_constraint_eval_dev(const int cta, const int n
   }
 }
 
+// ---- past information (k_p > 0) ------------------------------------------------------------
+// A Xbar_{t+1} = eta A Xbar_t + A(V S_c V^T) (eq. x_bar_def through the constraint values,
+// App. C): out[c] = eta ax[c] + <g_c, svec S_c>, eta read from the device scalars.
+template <typename T>
+__device__ __forceinline__ void k_constraint_axpy_dev(const int cta, const int ncta, int m, const int* USBS_RESTRICT con_ptr,
+                                                      const int* USBS_RESTRICT ent_i, const int* USBS_RESTRICT ent_j,
+                                                      const T* USBS_RESTRICT ent_v, const T* USBS_RESTRICT V,
+                                                      const double* USBS_RESTRICT S, const double* USBS_RESTRICT eta_dev,
+                                                      const double* USBS_RESTRICT ax, double* USBS_RESTRICT out) {
+  __shared__ double ssv[KSV];
+  __shared__ float ssf[KSV];
+  if (threadIdx.x == 0) {
+    svec8(S, ssv);
+    for (int u = 0; u < KSV; ++u) ssf[u] = (float)ssv[u];
+  }
+  __syncthreads();
+  const double eta = *eta_dev;
+  for (int64_t c = (int64_t)cta * blockDim.x + threadIdx.x; c < m; c += (int64_t)ncta * blockDim.x) {
+    T g[KSV];
+    build_g<T>(c, con_ptr, ent_i, ent_j, ent_v, V, g);
+    out[c] = eta * ax[c] + dot_svec<T>(g, ssv, ssf);
+  }
+}
+
+// W = [V Q_p | v_1 .. v_kc | 0] row by row (eq. v_next_def before its QR): the k_p past
+// columns V Q_p (Q_p: 8 x 8 FP64, its first k_p columns), then the first k_c Ritz vectors
+// at the candidate, then zeros.
+template <typename T>
+__device__ __forceinline__ void k_vnext_dev(const int cta, const int ncta, int n, const T* USBS_RESTRICT V,
+                                            const double* USBS_RESTRICT Qp, const T* USBS_RESTRICT U,
+                                            int kp, int kc, T* USBS_RESTRICT W) {
+  __shared__ T qs[64];
+  if (threadIdx.x < 64) qs[threadIdx.x] = (T)Qp[threadIdx.x];
+  __syncthreads();
+  for (int64_t i = (int64_t)cta * blockDim.x + threadIdx.x; i < n; i += (int64_t)ncta * blockDim.x) {
+    T v[8], u[8], w[8];
+    load8(V + 8 * i, v);
+    load8(U + 8 * i, u);
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      T acc = (T)0;
+      if (a < kp) {
+#pragma unroll
+        for (int b = 0; b < 8; ++b) acc += v[b] * qs[b * 8 + a];
+      } else if (a < kp + kc) {
+#pragma unroll
+        for (int b = 0; b < 8; ++b)
+          if (b == a - kp) acc = u[b];
+      }
+      w[a] = acc;
+    }
+    store8(W + 8 * i, w);
+  }
+}
+
 // ---- B = V^T Psi (8 x r) ------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ void k_vt_psi_dev(const int cta, const int ncta, int n, int r, const T* USBS_RESTRICT V,

@@ -343,8 +343,8 @@ __device__ __forceinline__ void k_ritz_f32_dev(DevLanczos* lz, int kc, double to
   float* A0 = reinterpret_cast<float*>(smem_raw);   // J x LD: T (scaled), rotated
   float* A1 = A0 + J * LD;                            // J x LD: the other buffer of A
   float* Vv = A1 + J * LD;                            // J x LD: accumulated rotations
-  float* Tc = Vv + J * LD;                            // J x LD: copy of T (unscaled)
-  float* Z = Tc + J * LD;                             // J x keep: T Y_keep (first: I - G)
+  float* Z = Vv + 2 * J * LD;                         // J x keep floats: I - G, then the FP64
+                                                      // keep x keep restarted matrix
   __shared__ float key[JMAX], dg[JMAX];
   __shared__ int order[JMAX];
   __shared__ float wsum[2][16];
@@ -384,7 +384,6 @@ __device__ __forceinline__ void k_ritz_f32_dev(DevLanczos* lz, int kc, double to
     const double x = lz->T[i * JMAX + j];
     const float xf = (float)x;
     A0[i * LD + j] = fscale ? xf * scf : (float)(x * scd);
-    Tc[i * LD + j] = xf;
     Vv[i * LD + j] = (i == j) ? 1.f : 0.f;
   }
   __syncthreads();
@@ -499,32 +498,46 @@ __device__ __forceinline__ void k_ritz_f32_dev(DevLanczos* lz, int kc, double to
   }
   __syncthreads();
   Y = Yn;
-  // Z = T Y_keep; restarted projected matrix Y_keep^T T Y_keep
+  // FP64 finish.  The FP32 rotations only serve to find the Ritz vectors; the quantities
+  // that leave the kernel are formed in FP64 from the FP64 projected matrix T and the kept
+  // vectors (their FP32 values, exact in FP64): Z = T Y_keep, the restarted projected
+  // matrix B = Y_keep^T Z, the Rayleigh quotients theta_i = y_i^T T y_i / y_i^T y_i and the
+  // residual norms.  A Rayleigh quotient of an approximate eigenvector with angle error e
+  // is off by O(e^2), so the Ritz values carry FP64 accuracy, not the FP32 of the rotations.
+  double* Yd = reinterpret_cast<double*>(Vv);                  // J x keep
+  double* Zd = reinterpret_cast<double*>(Y == A0 ? A1 : A0);   // J x keep
+  double* Bd = reinterpret_cast<double*>(Z);                   // keep x keep
+  for (int t = tid; t < J * keep; t += blockDim.x) Yd[t] = (double)Y[(t / keep) * LD + t % keep];
+  __syncthreads();
   for (int t = tid; t < J * keep; t += blockDim.x) {
     const int r = t / keep, i = t % keep;
-    float z = 0.f;
-    for (int c2 = 0; c2 < J; ++c2) z = fmaf(Tc[r * LD + c2], Y[c2 * LD + i], z);
-    Z[r * keep + i] = z;
+    const double* Tr = lz->T + r * JMAX;
+    double z = 0.0;
+    for (int c2 = 0; c2 < J; ++c2) z = fma(Tr[c2], Yd[c2 * keep + i], z);
+    Zd[t] = z;
+  }
+  __syncthreads();
+  for (int t = tid; t < keep * keep; t += blockDim.x) {
+    const int i = t / keep, j = t % keep;
+    if (j < i) continue;
+    double acc = 0.0;
+    for (int r = 0; r < J; ++r) acc = fma(Yd[r * keep + i], Zd[r * keep + j], acc);
+    Bd[i * keep + j] = acc;          // symmetric by construction: one value per pair
+    Bd[j * keep + i] = acc;
   }
   __syncthreads();
   for (int t = tid; t < JMAX * JMAX; t += blockDim.x) {
     const int i = t / JMAX, j = t % JMAX;
-    double v = 0.0;
-    if (i < keep && j < keep) {
-      float acc = 0.f;
-      for (int r = 0; r < J; ++r) acc = fmaf(Y[r * LD + i], Z[r * keep + j], acc);
-      v = (double)acc;
-    }
-    lz->T[t] = v;
+    lz->T[t] = (i < keep && j < keep) ? Bd[i * keep + j] : 0.0;
   }
   for (int t = tid; t < J * J; t += blockDim.x) {
     const int l = t / J, col = t % J;
     lz->Y[l * JMAX + col] = (double)Y[l * LD + col];
   }
   if (warp == 0) {
-    // Ritz values in T's units (the diagonal of A scaled back), then for the top k_c the
-    // Rayleigh quotients of the orthonormalised vectors and the residual norms
-    // ||T y_i - theta_i y_i||^2 + ||R_last E^T y_i||^2 (two orthogonal terms), in A's scale
+    // Ritz values in T's units (the diagonal of A scaled back, used for the order), then for
+    // the top k_c the FP64 Rayleigh quotients and residual norms
+    // ||T y_i - theta_i y_i||^2 + ||R_last E^T y_i||^2 (two orthogonal terms) of y_i / |y_i|
     for (int i = lane; i < J; i += 32) lz->theta[i] = ldexp((double)key[order[i]], esh);
     float m = 0.f;
     for (int i = lane; i < J; i += 32) m = fmaxf(m, fabsf(dg[i]));
@@ -533,23 +546,22 @@ __device__ __forceinline__ void k_ritz_f32_dev(DevLanczos* lz, int kc, double to
     double res = 0.0;
     if (lane < kc) {
       const int i = lane;
-      float zz = 0.f;
-      for (int r = 0; r < J; ++r) zz = fmaf(Y[r * LD + i], Z[r * keep + i], zz);
-      float s2 = 0.f;
-      const float inv = ldexpf(1.f, -max(-126, min(126, esh)));
+      double yy = 0.0;
+      for (int r = 0; r < J; ++r) yy = fma(Yd[r * keep + i], Yd[r * keep + i], yy);
+      const double th = Bd[i * keep + i] / yy;
+      double s2 = 0.0;
       for (int r = 0; r < J; ++r) {
-        const float e = (Z[r * keep + i] - zz * Y[r * LD + i]) * inv;
-        s2 = fmaf(e, e, s2);
+        const double e = Zd[r * keep + i] - th * Yd[r * keep + i];
+        s2 = fma(e, e, s2);
       }
       for (int a = 0; a < 8; ++a) {
-        float v = 0.f;
-        for (int c2 = a; c2 < 8; ++c2) v = fmaf((float)lz->Rlast[a * 8 + c2], Y[(J - 8 + c2) * LD + i], v);
-        v *= inv;
-        s2 = fmaf(v, v, s2);
+        double v = 0.0;
+        for (int c2 = a; c2 < 8; ++c2) v = fma(lz->Rlast[a * 8 + c2], Yd[(J - 8 + c2) * keep + i], v);
+        s2 = fma(v, v, s2);
       }
-      res = ldexp(sqrt((double)s2), max(-126, min(126, esh)));
+      res = sqrt(s2 / yy);
       lz->res[i] = res;
-      lz->theta[i] = (double)zz;
+      lz->theta[i] = th;
     }
     const bool ok = (lane >= kc) || (res <= tol * normest);
     const unsigned all_ok = __all_sync(FULL, ok);
@@ -1286,6 +1298,8 @@ __device__ __forceinline__ void k_finish_dev(DevScalars* sc, const DevLanczos* l
   }
   const double cx_new = sc->eta * sc->cx + cxS;
   const double tr_new = sc->eta * sc->tr + trS;
+  sc->cx_prev = sc->cx;
+  sc->tr_prev = sc->tr;
   const double bty = vec[36], axy = vec[37];
   double best = fmax(0.0, lamV);
   if (sc->has_eta) best = fmax(best, (sc->cx - axy) / sc->tr);
@@ -1305,6 +1319,8 @@ __device__ __forceinline__ void k_finish_dev(DevScalars* sc, const DevLanczos* l
   sc->tr_new = tr_new;
   sc->cx = cx_new;
   sc->tr = tr_new;
+  sc->cx_it = cx_new;
+  sc->tr_it = tr_new;
   sc->relgap = fabs(sc->f_y - cx_new) / (1.0 + fabs(cx_new));
   sc->relinf = sqrt(fmax(vec[38], 0.0)) / (1.0 + bnorm);
   sc->relinf_max = vec[39];
@@ -1323,8 +1339,141 @@ __device__ __forceinline__ void k_certify_dev(DevScalars* sc, const DevLanczos* 
   sc->f_cert = f;
   sc->lam_cert = lam;
   if (f > sc->f_y) sc->f_y = f;
-  sc->relgap = fabs(sc->f_y - sc->cx) / (1.0 + fabs(sc->cx));
+  sc->relgap = fabs(sc->f_y - sc->cx_it) / (1.0 + fabs(sc->cx_it));
   if (!isfinite(sc->f_y)) sc->status = USBS_ENUMERIC;
+}
+
+// ---- past information (k_p > 0; Sec. 3, eq. model_update_eigendecomposition) ----------------
+// All eigenpairs of a symmetric k x k matrix (k <= 8, row stride 8) in FP64 by one warp:
+// parallel cyclic Jacobi with circle ordering on 8 indices, four disjoint rotations per
+// round, until the off-diagonal mass of the k x k block is below 1e-30 of its total or 20
+// sweeps.  Aw is overwritten (its diagonal ends as the eigenvalues) and Vw receives the
+// eigenvectors as columns.  Entries outside the k x k block must be zero: a rotation of
+// such a pair is the identity.
+__device__ void warp_eig8_f64(double* Aw, double* Vw, int k) {
+  const int lane = threadIdx.x & 31;
+  for (int t = lane; t < 64; t += 32) Vw[t] = (t / 8 == t % 8) ? 1.0 : 0.0;
+  __syncwarp();
+  for (int sweep = 0; sweep < 20; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int t = lane; t < 64; t += 32) {
+      const double x = Aw[t];
+      tot += x * x;
+      if (t / 8 != t % 8) off += x * x;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(FULL, off, o);
+      tot += __shfl_xor_sync(FULL, tot, o);
+    }
+    if (!(off > 1e-30 * tot)) break;
+    for (int round = 0; round < 7; ++round) {
+      double c = 1.0, sv = 0.0;
+      int p = 0, q = 0;
+      if (lane < 4) {
+        const int pa = lane == 0 ? 0 : 1 + ((lane - 1 + round) % 7);
+        const int pb = 1 + ((7 - lane - 1 + round) % 7);
+        p = min(pa, pb);
+        q = max(pa, pb);
+        const double apq = Aw[p * 8 + q];
+        if (apq != 0.0) {
+          const double tau = (Aw[q * 8 + q] - Aw[p * 8 + p]) / (2.0 * apq);
+          const double t = fabs(tau) > 1e150 ? 0.5 / tau
+                                             : (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(tau * tau + 1.0));
+          c = 1.0 / sqrt(t * t + 1.0);
+          sv = t * c;
+        }
+      }
+      double cs[4], sn[4];
+      int pp[4], qq[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        cs[u] = __shfl_sync(FULL, c, u);
+        sn[u] = __shfl_sync(FULL, sv, u);
+        pp[u] = __shfl_sync(FULL, p, u);
+        qq[u] = __shfl_sync(FULL, q, u);
+      }
+      __syncwarp();
+      double na = 0.0, nb = 0.0, nc = 0.0, nd = 0.0;
+      const int k1 = (lane & 15) / 4, k2 = lane % 4;
+      if (lane < 16) {
+        const double a = Aw[pp[k1] * 8 + pp[k2]], b = Aw[pp[k1] * 8 + qq[k2]];
+        const double cc = Aw[qq[k1] * 8 + pp[k2]], d = Aw[qq[k1] * 8 + qq[k2]];
+        const double ra = cs[k1] * a - sn[k1] * cc, rb = cs[k1] * b - sn[k1] * d;
+        const double rc = sn[k1] * a + cs[k1] * cc, rd = sn[k1] * b + cs[k1] * d;
+        na = cs[k2] * ra - sn[k2] * rb;
+        nb = sn[k2] * ra + cs[k2] * rb;
+        nc = cs[k2] * rc - sn[k2] * rd;
+        nd = sn[k2] * rc + cs[k2] * rd;
+      }
+      const int kr = lane / 8, row = lane % 8;
+      const double vp = Vw[row * 8 + pp[kr]], vq = Vw[row * 8 + qq[kr]];
+      __syncwarp();
+      if (lane < 16) {
+        Aw[pp[k1] * 8 + pp[k2]] = na;
+        Aw[pp[k1] * 8 + qq[k2]] = nb;
+        Aw[qq[k1] * 8 + pp[k2]] = nc;
+        Aw[qq[k1] * 8 + qq[k2]] = nd;
+      }
+      Vw[row * 8 + pp[kr]] = cs[kr] * vp - sn[kr] * vq;
+      Vw[row * 8 + qq[kr]] = sn[kr] * vp + cs[kr] * vq;
+      __syncwarp();
+    }
+  }
+}
+
+// Split of S_{t+1} = Q_p L_p Q_p^T + Q_c L_c Q_c^T with (Q_p, L_p) its k_p largest
+// eigenpairs (eq. model_update_eigendecomposition).  Writes S_p, S_c and Q_p (8 x 8, the
+// k_p columns first) to sc, and the scalars of Xbar_{t+1} = eta Xbar_t + V S_c V^T (eq.
+// x_bar_def), summed from Xbar_t's and S_c's like the sketch, not by cancellation from
+// X_{t+1}'s: <C, Xbar> = eta <C, Xbar_t> + <V^T C V, S_c>, tr Xbar = eta tr Xbar_t + tr S_c.
+// One warp.
+__device__ __forceinline__ void k_kp_split_dev(DevScalars* sc, const double* USBS_RESTRICT red, int kdim, int kp) {
+  __shared__ double Aw[64], Vw[64], lam[8];
+  __shared__ int ord[8];
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x >= 32) return;
+  for (int t = lane; t < 64; t += 32) {
+    const int i = t / 8, j = t % 8;
+    Aw[t] = (i < kdim && j < kdim) ? 0.5 * (sc->S[i * 8 + j] + sc->S[j * 8 + i]) : 0.0;
+  }
+  __syncwarp();
+  warp_eig8_f64(Aw, Vw, kdim);
+  if (lane < 8) lam[lane] = Aw[lane * 9];
+  __syncwarp();
+  if (lane < kdim) {
+    // descending order under a strict total order (value, then index)
+    int rank = 0;
+    for (int u = 0; u < kdim; ++u)
+      if (lam[u] > lam[lane] || (lam[u] == lam[lane] && u < lane)) ++rank;
+    ord[rank] = lane;
+  }
+  __syncwarp();
+  for (int t = lane; t < 64; t += 32) {
+    const int i = t / 8, j = t % 8;
+    double sp = 0.0, scv = 0.0;
+    if (i < kdim && j < kdim) {
+      for (int u = 0; u < kdim; ++u) {
+        const int e = ord[u];
+        const double x = lam[e] * Vw[i * 8 + e] * Vw[j * 8 + e];
+        if (u < kp) sp += x; else scv += x;
+      }
+    }
+    sc->Sp[t] = sp;
+    sc->Sc[t] = scv;
+    sc->Qp[t] = (i < kdim && j < kp) ? Vw[i * 8 + ord[j]] : 0.0;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    const double* vc = red + RED_VC;
+    double ccx = 0.0, ctr = 0.0;
+    for (int p = 0; p < kdim; ++p) {
+      ctr += sc->Sc[p * 8 + p];
+      for (int q = 0; q < kdim; ++q) ccx += 0.5 * (vc[p * 8 + q] + vc[q * 8 + p]) * sc->Sc[p * 8 + q];
+    }
+    sc->cx = sc->eta * sc->cx_prev + ccx;
+    sc->tr = sc->eta * sc->tr_prev + ctr;
+    if (!isfinite(sc->cx) || !isfinite(sc->tr)) sc->status = USBS_ENUMERIC;
+  }
 }
 
 __device__ __forceinline__ void k_cold_dev(DevScalars* sc, const DevLanczos* lz, double alpha) {
@@ -1332,6 +1481,8 @@ __device__ __forceinline__ void k_cold_dev(DevScalars* sc, const DevLanczos* lz,
   sc->f_y = alpha * fmax(lz->theta[0], 0.0);
   sc->cx = 0.0;
   sc->tr = 0.0;
+  sc->cx_it = 0.0;
+  sc->tr_it = 0.0;
   sc->has_eta = 0;
   sc->t = 0;
   sc->status = 0;

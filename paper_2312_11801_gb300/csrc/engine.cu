@@ -384,6 +384,7 @@ static int build_ctx(Ctx* c, const HostProblem& hp, const float* Psi) {
   USBS_CUDA_TRY(c, cudaMallocHost(reinterpret_cast<void**>(&c->h_sc), sizeof(DevScalars)));
   USBS_CUDA_TRY(c, cudaMallocHost(reinterpret_cast<void**>(&c->h_lz), sizeof(DevLanczos)));
   USBS_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  tc_register(c);
   return USBS_OK;
 }
 
@@ -417,8 +418,8 @@ static int init_ctx(Ctx* c, int64_t n, int64_t m, int64_t nnzA, const usbs_param
                     const float* Psi) {
   if (p) c->prm = *p; else fill_defaults(&c->prm);
   usbs_params& q = c->prm;
-  if (q.k_p != 0) { c->err = "only k_p = 0 is supported"; return USBS_EINVAL; }
   if (q.k_c < 1 || q.k_c > KB) { c->err = "k_c must be in 1..8"; return USBS_EINVAL; }
+  if (q.k_p < 0 || q.k_c + q.k_p > KB) { c->err = "k_p must be >= 0 with k_c + k_p <= 8"; return USBS_EINVAL; }
   if (q.r < 0 || q.r > RMAX) { c->err = "r must be in 0..32"; return USBS_EINVAL; }
   if (q.r > 0 && !Psi) { c->err = "r > 0 needs Psi"; return USBS_EINVAL; }
   if (!(q.rho > 0.0) || !(q.beta > 0.0 && q.beta < 1.0)) { c->err = "rho > 0 and 0 < beta < 1"; return USBS_EINVAL; }
@@ -430,6 +431,9 @@ static int init_ctx(Ctx* c, int64_t n, int64_t m, int64_t nnzA, const usbs_param
   c->m = m;
   c->nnzA = nnzA;
   c->kc = q.k_c;
+  c->kp = q.k_p;
+  c->kdim = q.k_c + q.k_p;
+  c->kconv = q.k_c;
   c->r = q.r;
   c->fp64 = q.precision == USBS_PRECISION_FP64;
   c->alpha = q.alpha > 0.0 ? q.alpha : 2.0;
@@ -468,6 +472,8 @@ static int init_cuda(Ctx* c) {
   c->debug = dbg && dbg[0] == '1';
   const char* nospec = std::getenv("USBS_NO_SPECULATE");
   c->speculate = !(nospec && nospec[0] == '1');
+  const char* tcv = std::getenv("USBS_TCGEN05");
+  c->use_tc = tcv && tcv[0] == '1';
   if (q.stream) {
     c->stream = (cudaStream_t)q.stream;
     c->own_stream = false;
@@ -616,7 +622,7 @@ static int lanczos(Ctx* c, const double* y_dev, const void* start, void* out_vec
     lo->matvecs = matvecs;
     lo->converged = c->h_lz->converged;
     double mr = 0.0;
-    for (int i = 0; i < c->kc; ++i) mr = std::max(mr, c->h_lz->res[i]);
+    for (int i = 0; i < c->kconv; ++i) mr = std::max(mr, c->h_lz->res[i]);
     lo->max_res = mr;
   }
   c->total_matvecs += matvecs;
@@ -633,8 +639,12 @@ static int cold_start(Ctx* c) {
   USBS_CUDA_TRY(c, cudaMemsetAsync(c->ax, 0, sizeof(double) * c->m, c->stream));
   if (c->r) USBS_CUDA_TRY(c, cudaMemsetAsync(c->P, 0, sizeof(float) * c->n * c->r, c->stream));
   USBS_CUDA_TRY(c, cudaMemsetAsync(c->V, 0, es * 8 * c->n, c->stream));
+  // V_0: the top k_c + k_p eigenvectors of C (all of them converged)
   LanczosOut lo;
-  USBS_TRY(lanczos<T>(c, c->y, c->V, c->Vnew, &lo));
+  c->kconv = c->kdim;
+  const int rc = lanczos<T>(c, c->y, c->V, c->Vnew, &lo);
+  c->kconv = c->kc;
+  USBS_TRY(rc);
   std::swap(c->V, c->Vnew);
   launch_cold(c);
   c->started = true;
@@ -652,13 +662,13 @@ static void fill_info(Ctx* c, const DevScalars& s, int matvecs, usbs_step_info* 
   info->f_cand = s.f_cand;
   info->f_hat = s.f_hat;
   info->lambda_max = s.lam_max;
-  info->cx = s.cx;
-  info->trx = s.tr;
+  info->cx = s.cx_it;
+  info->trx = s.tr_it;
   info->eta = s.eta;
   info->relgap = s.relgap;
   info->relinf = s.relinf;
   info->relinf_max = s.relinf_max;
-  info->objective = s.cx * c->c_scale * c->tau;
+  info->objective = s.cx_it * c->c_scale * c->tau;
   info->dual_bound = s.f_y * c->c_scale * c->tau;
 }
 
@@ -705,9 +715,24 @@ static int step_impl(Ctx* c, usbs_step_info* info) {
   USBS_TRY(lanczos<T>(c, c->ycand, c->V, c->Vnew, &lo));
   launch_finish(c);
   launch_commit(c);
-  if (c->r)
-    Bulk<T>::sketch_update(c, c->V, DEV_FIELD(c->sc, DevScalars, S, double), c->red + RED_SK, c->P,
-                           c->Psi, DEV_FIELD(c->sc, DevScalars, eta, double), 0.0);
+  if (c->kp == 0) {
+    // model update with k_p = 0: Xbar_{t+1} = X_{t+1}, V_{t+1} = the top k_c Ritz vectors
+    if (c->r)
+      Bulk<T>::sketch_update(c, c->V, DEV_FIELD(c->sc, DevScalars, S, double), c->red + RED_SK, c->P,
+                             c->Psi, DEV_FIELD(c->sc, DevScalars, eta, double), 0.0);
+  } else {
+    // past information (Sec. 3): S = S_p + S_c; Xbar_{t+1} = eta Xbar_t + V S_c V^T
+    // (eq. x_bar_def) through <C, Xbar>, tr Xbar, A Xbar and the sketch; V_{t+1} = an
+    // orthonormal basis of [V Q_p, v_1..v_kc] (eq. v_next_def) by Cholesky QR
+    launch_kp_split(c);
+    if (c->r)
+      Bulk<T>::sketch_update(c, c->V, DEV_FIELD(c->sc, DevScalars, Sc, double), c->red + RED_SK, c->P,
+                             c->Psi, DEV_FIELD(c->sc, DevScalars, eta, double), 0.0);
+    Bulk<T>::constraint_axpy(c, c->V, DEV_FIELD(c->sc, DevScalars, Sc, double),
+                             DEV_FIELD(c->sc, DevScalars, eta, double), c->ax, c->axnew);
+    Bulk<T>::vnext(c, c->V, DEV_FIELD(c->sc, DevScalars, Qp, double), c->Vnew, c->W);
+    orth_block<T>(c, (T*)c->Q, 0, (T*)c->W, (T*)c->Vnew, -1, 0, 0);
+  }
   std::swap(c->V, c->Vnew);
   std::swap(c->ax, c->axnew);
   USBS_TRY(check_launch(c, "usbs_step"));
@@ -742,8 +767,10 @@ static int certify_impl(Ctx* c, double* residual, int* matvecs) {
   c->keep = J / 2;
   c->prm.lanczos_restarts = c->prm.certify_restarts;
   c->prm.lanczos_tol = c->prm.certify_tol;
+  c->kconv = 1;     // f(y) needs lambda_max alone
   LanczosOut lo;
   const int rc = lanczos<T>(c, c->y, c->V, c->Vnew, &lo);
+  c->kconv = c->kc;
   c->J = J0;
   c->keep = keep0;
   c->prm.lanczos_restarts = R0;
@@ -994,7 +1021,7 @@ int usbs_get_primal_constraints(usbs_ctx* ctx, double* ax) {
 int64_t usbs_state_size(const usbs_ctx* ctx) {
   if (!ctx) return -1;
   const Ctx* c = reinterpret_cast<const Ctx*>(ctx);
-  return 2 * c->m + 3 + c->n * c->kc + c->n * c->r;
+  return 2 * c->m + 3 + c->n * c->kdim + c->n * c->r;
 }
 
 int usbs_get_state(usbs_ctx* ctx, double* st) {
@@ -1017,13 +1044,13 @@ int usbs_get_state(usbs_ctx* ctx, double* st) {
   std::vector<unsigned char> buf(es * 8 * n);
   USBS_CUDA_TRY(c, cudaMemcpy(buf.data(), c->V, buf.size(), cudaMemcpyDeviceToHost));
   for (int64_t i = 0; i < n; ++i)
-    for (int a = 0; a < c->kc; ++a)
-      Vo[i * c->kc + a] = c->fp64 ? reinterpret_cast<double*>(buf.data())[i * 8 + a]
-                                  : (double)reinterpret_cast<float*>(buf.data())[i * 8 + a];
+    for (int a = 0; a < c->kdim; ++a)
+      Vo[i * c->kdim + a] = c->fp64 ? reinterpret_cast<double*>(buf.data())[i * 8 + a]
+                                    : (double)reinterpret_cast<float*>(buf.data())[i * 8 + a];
   if (c->r) {
     std::vector<float> P((size_t)n * c->r);
     USBS_CUDA_TRY(c, cudaMemcpy(P.data(), c->P, P.size() * sizeof(float), cudaMemcpyDeviceToHost));
-    double* Po = Vo + n * c->kc;
+    double* Po = Vo + n * c->kdim;
     for (size_t u = 0; u < P.size(); ++u) Po[u] = (double)P[u] * c->tau;
   }
   return USBS_OK;
@@ -1047,23 +1074,25 @@ int usbs_set_state(usbs_ctx* ctx, const double* st) {
   c->h_sc->cx = st[2 * m] / (c->c_scale * c->tau);
   c->h_sc->tr = st[2 * m + 1] / c->tau;
   c->h_sc->f_y = st[2 * m + 2] / (c->c_scale * c->tau);
+  c->h_sc->cx_it = c->h_sc->cx;
+  c->h_sc->tr_it = c->h_sc->tr;
   c->h_sc->status = 0;
   USBS_CUDA_TRY(c, cudaMemcpyAsync(c->sc, c->h_sc, sizeof(DevScalars), cudaMemcpyHostToDevice, c->stream));
   const double* Vi = st + 2 * m + 3;
   if (c->fp64) {
     std::vector<double> Vb((size_t)8 * n, 0.0);
     for (int64_t i = 0; i < n; ++i)
-      for (int a = 0; a < c->kc; ++a) Vb[i * 8 + a] = Vi[i * c->kc + a];
+      for (int a = 0; a < c->kdim; ++a) Vb[i * 8 + a] = Vi[i * c->kdim + a];
     USBS_CUDA_TRY(c, cudaMemcpyAsync(c->V, Vb.data(), Vb.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   } else {
     std::vector<float> Vb((size_t)8 * n, 0.f);
     for (int64_t i = 0; i < n; ++i)
-      for (int a = 0; a < c->kc; ++a) Vb[i * 8 + a] = (float)Vi[i * c->kc + a];
+      for (int a = 0; a < c->kdim; ++a) Vb[i * 8 + a] = (float)Vi[i * c->kdim + a];
     USBS_CUDA_TRY(c, cudaMemcpyAsync(c->V, Vb.data(), Vb.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
   }
   if (c->r) {
     std::vector<float> P((size_t)n * c->r);
-    const double* Pi = Vi + n * c->kc;
+    const double* Pi = Vi + n * c->kdim;
     for (size_t u = 0; u < P.size(); ++u) P[u] = (float)(Pi[u] / c->tau);
     USBS_CUDA_TRY(c, cudaMemcpyAsync(c->P, P.data(), P.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
   }
@@ -1101,7 +1130,7 @@ int usbs_grow(usbs_ctx* ctx_old, usbs_ctx** out, int64_t n, const int64_t* C_row
   const double* ax0 = y0 + m0;
   const double cx0 = st0[2 * m0], tr0 = st0[2 * m0 + 1];
   const double* V0 = st0.data() + 2 * m0 + 3;
-  const double* P0 = V0 + n0 * o->kc;
+  const double* P0 = V0 + n0 * o->kdim;
   // old C (problem units): merged pattern and diagonal
   std::vector<int> orow(n0 + 1), ocol(o->nnz_off);
   std::vector<double> oval(o->nnz_off), odiag(n0);
@@ -1182,9 +1211,9 @@ int usbs_grow(usbs_ctx* ctx_old, usbs_ctx** out, int64_t n, const int64_t* C_row
   }
   double* V = st.data() + 2 * m + 3;
   for (int64_t i = 0; i < n0; ++i)
-    for (int a = 0; a < c->kc; ++a) V[i * c->kc + a] = V0[i * o->kc + a];
+    for (int a = 0; a < c->kdim; ++a) V[i * c->kdim + a] = V0[i * o->kdim + a];
   if (c->r && ok_primal) {
-    double* P = V + n * c->kc;
+    double* P = V + n * c->kdim;
     for (int64_t i = 0; i < n0; ++i)
       for (int a = 0; a < c->r; ++a) P[i * c->r + a] = P0[i * o->r + a];
   }

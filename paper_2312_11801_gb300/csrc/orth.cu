@@ -105,9 +105,19 @@ int orth_grid(Ctx* c, int64_t rows, const void* kernel, size_t smem) {
   return (int)(g < 1 ? 1 : g);
 }
 
+// FP32 contexts take the tcgen05 tiles (tc_orth.cu) when their buffers have tensor maps
+template <typename T>
+static bool on_tc(const Ctx* c) {
+  return sizeof(T) == 4 && c->use_tc && !c->tma.empty();
+}
+
 template <typename T>
 int Orth<T>::proj(Ctx* c, const void* Qb, int nb, const void* W, const int* mask) {
   USBS_LAUNCH_B(c, USBS_KIND_REORTH, mask ? 0.0 : 8.0 * sizeof(T) * c->n * (nb + 1));
+  if (on_tc<T>(c)) {
+    const int g = tc_proj(c, Qb, nb, W, mask);
+    if (g > 0) return g;
+  }
   set_attrs<T>();
   // the epilogue reuses the stage buffers for its warp partials
   const size_t sm = std::max(tile_smem<T>(nb, 0), sizeof(double) * 8 * 512);
@@ -120,6 +130,10 @@ int Orth<T>::proj(Ctx* c, const void* Qb, int nb, const void* W, const int* mask
 template <typename T>
 int Orth<T>::gram_xy(Ctx* c, const void* X, const void* Y) {
   USBS_LAUNCH_B(c, USBS_KIND_REORTH, 16.0 * sizeof(T) * c->n);
+  if (on_tc<T>(c)) {
+    const int g = tc_proj(c, X, 1, Y, nullptr);
+    if (g > 0) return g;
+  }
   set_attrs<T>();
   const size_t sm = std::max(tile_smem<T>(1, 0), sizeof(double) * 8 * 512);
   const int g = orth_grid(c, c->n, (const void*)k_tproj<T>, sm);
@@ -131,6 +145,10 @@ int Orth<T>::gram_xy(Ctx* c, const void* X, const void* Y) {
 template <typename T>
 int Orth<T>::update(Ctx* c, const void* Qb, int nb, void* W, const int* mask) {
   USBS_LAUNCH_B(c, USBS_KIND_REORTH_UPDATE, mask ? 0.0 : 8.0 * sizeof(T) * c->n * (nb + 2));
+  if (on_tc<T>(c)) {
+    const int g = tc_update(c, Qb, nb, W, mask);
+    if (g > 0) return g;
+  }
   set_attrs<T>();
   // the epilogue reuses the stage buffers for its warp partials: FP32 (tensor cores)
   // 8 warps x 5 pairs x 32 x 4 floats; FP64 8 warps x (32 or 64) slots x 16 doubles
@@ -147,6 +165,7 @@ template <typename T>
 void Orth<T>::finalize(Ctx* c, const void* Qb, int nb, const void* W, void* out, const int* mask,
                        uint64_t seed) {
   USBS_LAUNCH_B(c, USBS_KIND_REORTH_FINAL, mask ? 0.0 : 8.0 * sizeof(T) * c->n * (nb + 2));
+  if (on_tc<T>(c) && tc_final(c, Qb, nb, W, out, mask, seed)) return;
   set_attrs<T>();
   const size_t sm = tile_smem<T>(nb, 8 * 64 + 64);
   k_tfinalize<T><<<orth_grid(c, c->n, (const void*)k_tfinalize<T>, sm), 256, sm, c->stream>>>(
@@ -158,6 +177,7 @@ template <typename T>
 void Orth<T>::restart(Ctx* c, const void* Qb, int J, int nout, const double* Y, void* out,
                       const void* resid, int resid_slot) {
   USBS_LAUNCH_B(c, USBS_KIND_RESTART, 8.0 * sizeof(T) * c->n * (J / 8 + nout + (resid ? 2 : 0)));
+  if (on_tc<T>(c) && tc_restart(c, Qb, J, nout, Y, out, resid, resid_slot)) return;
   set_attrs<T>();
   const size_t sm = sizeof(T) * (2 * (size_t)(J / 8) * BlockStride<T>::value + (size_t)J * nout * 8);
   k_trestart<T><<<orth_grid(c, c->n, (const void*)k_trestart<T>, sm), 256, sm, c->stream>>>(

@@ -51,6 +51,10 @@ __global__ void k_certify(DevScalars* sc, const DevLanczos* lz, const double* __
   k_certify_dev(sc, lz, red, alpha);
 }
 
+__global__ void k_kp_split(DevScalars* sc, const double* __restrict__ red, int kdim, int kp) {
+  k_kp_split_dev(sc, red, kdim, kp);
+}
+
 __global__ void k_cold(DevScalars* sc, const DevLanczos* lz, double alpha) {
   k_cold_dev(sc, lz, alpha);
 }
@@ -100,11 +104,11 @@ static void launch_ritz_t(Ctx* c, int J, int max_sweeps, double eps, int spec) {
   const size_t sm = ritz_smem(sizeof(S), J);
   const int threads = J >= 64 ? 512 : 256;
   if (J == 16)
-    k_ritz<S, 16><<<1, threads, sm, c->stream>>>(c->lz, c->kc, c->prm.lanczos_tol, max_sweeps, eps, spec);
+    k_ritz<S, 16><<<1, threads, sm, c->stream>>>(c->lz, c->kconv, c->prm.lanczos_tol, max_sweeps, eps, spec);
   else if (J == 32)
-    k_ritz<S, 32><<<1, threads, sm, c->stream>>>(c->lz, c->kc, c->prm.lanczos_tol, max_sweeps, eps, spec);
+    k_ritz<S, 32><<<1, threads, sm, c->stream>>>(c->lz, c->kconv, c->prm.lanczos_tol, max_sweeps, eps, spec);
   else
-    k_ritz<S, 64><<<1, threads, sm, c->stream>>>(c->lz, c->kc, c->prm.lanczos_tol, max_sweeps, eps, spec);
+    k_ritz<S, 64><<<1, threads, sm, c->stream>>>(c->lz, c->kconv, c->prm.lanczos_tol, max_sweeps, eps, spec);
 }
 
 void launch_ritz(Ctx* c, int J, int keep, int spec) {
@@ -123,17 +127,20 @@ void launch_ritz(Ctx* c, int J, int keep, int spec) {
 
 void launch_ipm(Ctx* c, int first_pass) {
   USBS_LAUNCH(c, USBS_KIND_SMALL);
-  k_ipm<<<1, 256, 0, c->stream>>>(c->sc, c->red, c->kc, c->alpha, c->prm.rho, c->prm.ipm_mu_tol,
+  k_ipm<<<1, 256, 0, c->stream>>>(c->sc, c->red, c->kdim, c->alpha, c->prm.rho, c->prm.ipm_mu_tol,
                                   c->prm.ipm_max_iter, first_pass);
 }
 
 void launch_finish(Ctx* c) {
   USBS_LAUNCH(c, USBS_KIND_SMALL);
-  k_finish<<<1, 32, 0, c->stream>>>(c->sc, c->lz, c->red, c->kc, c->alpha, c->prm.beta, c->bnorm);
+  k_finish<<<1, 32, 0, c->stream>>>(c->sc, c->lz, c->red, c->kdim, c->alpha, c->prm.beta, c->bnorm);
 }
 
 void launch_certify(Ctx* c) {
   USBS_LAUNCH(c, USBS_KIND_SMALL); k_certify<<<1, 32, 0, c->stream>>>(c->sc, c->lz, c->red, c->alpha); }
+
+void launch_kp_split(Ctx* c) {
+  USBS_LAUNCH(c, USBS_KIND_SMALL); k_kp_split<<<1, 32, 0, c->stream>>>(c->sc, c->red, c->kdim, c->kp); }
 
 void launch_cold(Ctx* c) {
   USBS_LAUNCH(c, USBS_KIND_SMALL); k_cold<<<1, 32, 0, c->stream>>>(c->sc, c->lz, c->alpha); }

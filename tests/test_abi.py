@@ -59,7 +59,8 @@ def _expect_einval(U, prob, match, **kw):
 
 def test_invalid_arguments_rejected_on_the_host(U):
     p = I.maxcut_er(40, 4, seed=1)
-    _expect_einval(U, p, "k_p", k_p=1)
+    _expect_einval(U, p, "k_p", k_p=1)          # k_c = 8 leaves no room in V's 8 columns
+    _expect_einval(U, p, "k_p", k_c=6, k_p=-1)
     _expect_einval(U, p, "k_c", k_c=9)
     _expect_einval(U, p, "certify_restarts", certify_restarts=-1)
     _expect_einval(U, p, "Psi", r=4)

@@ -1,0 +1,228 @@
+"""Parity at the grid shapes of the full-size workloads, through the C ABI.
+
+The small parity cases give every CTA of a tiled launch a single tile and leave the
+grid-stride loops of the row kernels unused.  These cases are large enough that
+- the Gram-Schmidt and restart tiles run several tiles per CTA (n = 160,000: 1,250
+  tiles of 128 rows over at most 304 CTAs in mixed precision, 2,500 tiles of 64 rows in
+  FP64), so the double-buffered stages, their mbarrier phases and the per-CTA partial
+  sums over many tiles are compared with the oracle;
+- the SpMM, the A*(y) set-up and the per-constraint kernels wrap their grid-stride loops
+  (at most 8 CTAs of 256 threads per SM, i.e. 311,296 rows, and 608 CTAs of 128 or 256
+  constraints for the reducing kernels).
+Expected values come from tests/golden/oracle_large.json, written by
+tests/golden/make_large_golden.py (oracle only), or from the oracle's operators directly.
+
+Tolerances:
+- eigenvalues: 1e-5 (mixed) and 1e-9 (FP64) relative to max(|lambda|, ||M||_2) as in
+  the smaller cases, and relative to |lambda| itself for the top k_c values;
+- operators: FP64 1e-12, mixed 2e-5 relative (about 2^-24 per rounding times the
+  accumulation length), constraint sums 10x that;
+- the mixed step trajectory: 2e-4 (1 + |x|) per scaled quantity (see the test).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import usbs as OU
+from paper_2312_11801_gb300 import instances as I
+from tests.gpu_util import bulk_dtype, gpu_modules, rel_err
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _golden(name):
+    return json.load(open(os.path.join(HERE, "golden", "oracle_large.json")))[name]
+
+
+_PROBLEMS = {
+    "torus400": lambda: I.maxcut_torus(400, seed=7, signed=True),
+    "clust100k": lambda: I.clustering_sdp(100_000, 400_000, seed=3),
+    "er6000": lambda: I.maxcut_er(6000, 6.0, 2),
+}
+
+
+@pytest.fixture(scope="module")
+def mods():
+    return gpu_modules()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("case", ["torus400_eig", "clust100k_eig"])
+def test_extreme_eigs_full_size(mods, case, precision):
+    """a1-a4 at n = 160,000 and 100,000: top-8 eigenvalues of C - A*(y) against the
+    oracle's block Lanczos run to a 1e-11 residual."""
+    torch, U = mods
+    g = _golden(case)
+    prob = _PROBLEMS[g["problem"]]()
+    y_s = I.dual_sample(prob, seed=g["dual_seed"])
+    ref = np.asarray(g["evals"])
+    tol = 1e-9 if precision == 0 else 1e-5
+    ltol = 1e-11 if precision == 0 else 3e-7
+    with U.usbs_create(prob, precision=precision, lanczos_restarts=400, lanczos_tol=ltol) as ctx:
+        c_scale, _ = U.usbs_scaling(ctx)
+        evals, _, info = U.usbs_extreme_eigs(ctx, y=y_s * c_scale, want_vecs=False)
+    err = np.abs(evals - ref)
+    assert np.all(err <= tol * np.maximum(np.abs(ref), g["norm2"])), (err, info)
+    assert np.all(err <= tol * np.abs(ref)), (err / np.abs(ref), info)
+
+
+@pytest.mark.parametrize("case", ["torus400_eig", "clust100k_eig"])
+def test_extreme_eigs_default_budget(mods, case, record_property):
+    """The solver's own eigen-solve budget (mixed, 64-column basis, 10 restarts, 1e-6):
+    the achieved top-eigenvalue error is recorded.  Asserted: a Ritz value never exceeds
+    lambda_max (up to the FP32 rounding of the projected matrix, 1e-5 of ||M||), and a loose
+    1e-2 sanity bound."""
+    torch, U = mods
+    g = _golden(case)
+    prob = _PROBLEMS[g["problem"]]()
+    y_s = I.dual_sample(prob, seed=g["dual_seed"])
+    ref = np.asarray(g["evals"])
+    with U.usbs_create(prob, precision=1) as ctx:
+        c_scale, _ = U.usbs_scaling(ctx)
+        evals, _, info = U.usbs_extreme_eigs(ctx, y=y_s * c_scale, want_vecs=False)
+    rel = float(abs(evals[0] - ref[0]) / abs(ref[0]))
+    record_property("top_eig_rel_err_default_budget", rel)
+    record_property("restarts_used", info["cycles"])
+    print(f"{case}: top eigenvalue relative error at the default budget {rel:.3e}, "
+          f"{info['cycles']} cycles, max residual {info['max_residual']:.3e}")
+    assert evals[0] <= ref[0] + 1e-5 * g["norm2"]     # the mixed-precision parity bound
+    assert rel <= 1e-2
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_matmul_wraps_grid(mods, precision):
+    """a1 + a2 at n = 490,000 (700 x 700 torus): the SpMM and diagonal set-up loop
+    over their grid."""
+    torch, U = mods
+    prob = I.maxcut_torus(700, seed=2, signed=True)
+    sp_ = OU.scale_problem(prob)
+    rng = np.random.default_rng(3)
+    y = rng.standard_normal(prob.m) * 0.3 / np.sqrt(prob.n)
+    X = rng.standard_normal((prob.n, 8))
+    dt = bulk_dtype(torch, precision)
+    Xr = torch.tensor(X, dtype=dt).double().numpy()
+    ref = OU.slack_matrix(sp_, y) @ Xr
+    with U.usbs_create(prob, precision=precision) as ctx:
+        Yd = torch.empty((prob.n, 8), dtype=dt, device="cuda")
+        U.usbs_op_matmul(ctx, torch.tensor(y, dtype=torch.float64, device="cuda"),
+                         torch.tensor(X, dtype=dt, device="cuda"), Yd)
+        torch.cuda.synchronize()
+        got = Yd.double().cpu().numpy()
+    assert rel_err(got, ref) <= (1e-12 if precision == 0 else 2e-5)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_matmul_offdiag_scatter_wraps_grid(mods, precision):
+    """a1 with off-diagonal A*(y) entries (n = 400,000, 1.2M edge inequalities): the
+    effective-value set-up and the SpMM both loop over their grid."""
+    torch, U = mods
+    prob = I.clustering_sdp(400_000, 1_200_000, seed=4)
+    sp_ = OU.scale_problem(prob)
+    y = I.dual_sample(prob, seed=5)
+    X = np.random.default_rng(6).standard_normal((prob.n, 8))
+    dt = bulk_dtype(torch, precision)
+    Xr = torch.tensor(X, dtype=dt).double().numpy()
+    ref = OU.slack_matrix(sp_, y) @ Xr
+    with U.usbs_create(prob, precision=precision) as ctx:
+        Yd = torch.empty((prob.n, 8), dtype=dt, device="cuda")
+        U.usbs_op_matmul(ctx, torch.tensor(y, dtype=torch.float64, device="cuda"),
+                         torch.tensor(X, dtype=dt, device="cuda"), Yd)
+        torch.cuda.synchronize()
+        got = Yd.double().cpu().numpy()
+    assert rel_err(got, ref) <= (1e-12 if precision == 0 else 2e-5)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_constraint_eval_wraps_grid(mods, precision):
+    """a9 with m = 600,000 constraints (n = 200,000, 400,000 edge rows)."""
+    torch, U = mods
+    prob = I.clustering_sdp(200_000, 400_000, seed=8)
+    sp_ = OU.scale_problem(prob)
+    rng = np.random.default_rng(9)
+    V, _ = np.linalg.qr(rng.standard_normal((prob.n, 8)))
+    S = rng.standard_normal((8, 8)); S = S + S.T
+    dt = bulk_dtype(torch, precision)
+    Vr = torch.tensor(V, dtype=dt).double().numpy()
+    ref = OU.A_lowrank(sp_, Vr, S)
+    with U.usbs_create(prob, precision=precision) as ctx:
+        z = torch.zeros(prob.m, dtype=torch.float64, device="cuda")
+        U.usbs_op_constraint_eval(ctx, torch.tensor(V, dtype=dt, device="cuda"),
+                                  torch.tensor(S, dtype=torch.float64, device="cuda"), z)
+        torch.cuda.synchronize()
+        got = z.cpu().numpy()
+    assert rel_err(got, ref) <= (1e-11 if precision == 0 else 2e-4)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_sketch_update_full_size(mods, precision):
+    """a10 at n = 499,849 (the 707 x 707 torus), r = 32: V^T Psi over 608 CTAs (many rows
+    each) and the update over the whole grid."""
+    torch, U = mods
+    r = 32
+    prob = I.maxcut_torus(707, seed=1)
+    n = prob.n
+    rng = np.random.default_rng(10)
+    psi = I.gaussian_psi(n, r, seed=4)
+    V, _ = np.linalg.qr(rng.standard_normal((n, 8)))
+    S = rng.standard_normal((8, 8)); S = S @ S.T
+    P0 = rng.standard_normal((n, r)).astype(np.float32)
+    eta = 0.61
+    dt = bulk_dtype(torch, precision)
+    Vr = torch.tensor(V, dtype=dt).double().numpy()
+    ref = eta * P0.astype(np.float64) + Vr @ (S @ (Vr.T @ psi.astype(np.float64)))
+    with U.usbs_create(prob, psi=psi, r=r, precision=precision) as ctx:
+        Pd = torch.tensor(P0, device="cuda")
+        U.usbs_op_sketch_update(ctx, torch.tensor(V, dtype=dt, device="cuda"),
+                                torch.tensor(S, dtype=torch.float64, device="cuda"),
+                                torch.tensor(psi, device="cuda"), Pd, eta)
+        torch.cuda.synchronize()
+        got = Pd.double().cpu().numpy()
+    assert rel_err(got, ref) <= 2e-5
+
+
+def test_step_trajectory_mixed_torus400(mods):
+    """Six iterations of Algorithm 1 in mixed precision on the 400 x 400 torus
+    (n = m = 160,000, rho = 0.01) against the FP64 oracle's.  Every row kernel and tile
+    kernel runs here at a grid that wraps (G^T G over 608 CTAs of 128 constraints,
+    Gram-Schmidt over 4-5 tiles per CTA).  The eigen solves stop at a 3e-7 relative
+    residual, and V, the SpMM and the Gram-Schmidt are FP32: after a step, f(y), <C,X>,
+    tr X, lambda_max and the infeasibility agree with the oracle to about 1e-5 relative,
+    and a few steps compound that; 2e-4 (1 + |x|) in scaled units bounds six steps."""
+    torch, U = mods
+    g = _golden("torus400_traj")
+    prob = _PROBLEMS[g["problem"]]()
+    with U.usbs_create(prob, precision=1, rho=g["rho"], lanczos_restarts=400,
+                       lanczos_tol=3e-7) as ctx:
+        for row in g["steps"]:
+            s = U.usbs_step(ctx)
+            assert s["descent"] == row["descent"], (row["t"], s, row)
+            for kg, ko in [("f_y", "f_y"), ("cx", "cx"), ("trx", "trx"),
+                           ("lambda_max", "lambda_max"), ("relinf", "relinf"), ("f_hat", "f_hat")]:
+                tol = 2e-4 * (1 + abs(row[ko]))
+                assert abs(s[kg] - row[ko]) <= tol, (row["t"], kg, s[kg], row[ko])
+
+
+def test_solve_mixed_er6000(mods):
+    """A mixed-precision solve at n = 6000 to both gates <= 1e-3 against the oracle's
+    solve to 1e-4 (rho = 0.1): each dual bound lies above the other side's primal value
+    up to the two gaps, and the objectives agree within the sum of the gaps."""
+    torch, U = mods
+    g = _golden("er6000_solve")
+    prob = _PROBLEMS[g["problem"]]()
+    with U.usbs_create(prob, precision=1, rho=g["rho"], max_iters=3000) as ctx:
+        res = U.usbs_solve(ctx, tol=1e-3)
+    last = res["last"]
+    assert res["converged"], (res["iters"], last["relgap"], last["relinf"])
+    cx, f = last["cx"], last["f_y"]
+    cx_o, f_o = g["cx_scaled"], g["f_scaled"]
+    slack_g = 1e-3 * (1 + abs(cx))
+    slack_o = max(g["relgap"], g["relinf"]) * (1 + abs(cx_o))
+    assert f >= cx_o - slack_o - slack_g, (f, cx_o)
+    assert f_o >= cx - slack_g - slack_o, (f_o, cx)
+    assert abs(cx - cx_o) <= slack_g + slack_o, (cx, cx_o)
+    # objective-relative agreement, for the record
+    print(f"er6000: GPU objective {last['objective']:.6f}, oracle {g['objective']:.6f}, "
+          f"relative difference {abs(last['objective'] - g['objective']) / abs(g['objective']):.2e}")
