@@ -181,14 +181,20 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc(const __grid_constant__ CUten
     const int s = it & 1;
     const int tile = blockIdx.x + it * gridDim.x;
     float* st = reinterpret_cast<float*>(smem + L.stage + s * L.stage_bytes);
-    bool ok = tc::bar_wait(&bars[s], (it >> 1) & 1);
-    if (ok && p2_out) ok = tc::bar_wait(&bars[3], ph2);
+    // one thread waits (the others sleep in the barrier); afterwards every thread observes
+    // the completed phases itself (a test that returns at once) to acquire their writes
+    bool ok = true;
+    if (tid == 0) {
+      ok = tc::bar_wait(&bars[s], (it >> 1) & 1);
+      if (ok && p2_out) ok = tc::bar_wait(&bars[3], ph2);
+    }
     if (!__syncthreads_and(ok)) { aborted = true; break; }
-    if (p2_out) { p2_out = false; ph2 ^= 1; }
+    tc::bar_test(&bars[s], (it >> 1) & 1);
+    if (p2_out) { tc::bar_test(&bars[3], ph2); p2_out = false; ph2 ^= 1; }
     tc::fence_after_sync();
 
     // ---- split pass ----
-    if (MODE != TC_PROJ) {
+    if (MODE == TC_FINAL || MODE == TC_RESTART) {
       // lo of every Q element, in the staged (swizzled) layout
       const int nvec = nb * TC_TR * 2;
       for (int v = tid; v < nvec; v += TC_THREADS) {
@@ -198,20 +204,27 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc(const __grid_constant__ CUten
         y.z = tc::tf32_lo(x.z, tc::tf32_hi(x.z)); y.w = tc::tf32_lo(x.w, tc::tf32_hi(x.w));
         reinterpret_cast<float4*>(lo)[v] = y;
       }
-    }
-    if (MODE == TC_PROJ || MODE == TC_UPDATE) {
+    } else {
       // transposed hi / lo atoms: atom (ks, h, b) holds, as its row m and column k, the value
-      // of column m of block b at tile row 8 ks + k.  Both the reads (8 rows x 4 columns of
-      // the swizzled tile) and the writes (128 contiguous bytes) of a warp are free of bank
-      // conflicts.
-      const int natom = (MODE == TC_PROJ ? nb + 1 : nb) * 16;
-      for (int at = tq; at < natom; at += 4) {
-        const int b = at >> 4, ks = at & 15;
-        const float x = st[b * 1024 + ks * 64 + rd_off];
-        const float hi = tc::tf32_hi(x);
-        float* dst = T + ks * tg + b * 64 + wr_off;
-        dst[0] = hi;
-        dst[(nb + 1) * 64] = tc::tf32_lo(x, hi);
+      // of column m of block b at tile row 8 ks + k (and the update also writes the lo of the
+      // element in the staged layout for phase 1).  Both the reads (8 rows x 4 columns of the
+      // swizzled tile) and the transposed writes (128 contiguous bytes) of a warp are free of
+      // bank conflicts.
+      const int nblk = MODE == TC_PROJ ? nb + 1 : nb;
+      const int tlo = (nb + 1) * 64;
+      for (int b = 0; b < nblk; ++b) {
+        const float* src = st + b * 1024 + tq * 64 + rd_off;
+        float* lrow = lo + b * 1024 + tq * 64 + rd_off;
+        float* dst = T + tq * tg + b * 64 + wr_off;
+#pragma unroll
+        for (int ks = 0; ks < 16; ks += 4) {
+          const float x = src[ks * 64];
+          const float hi = tc::tf32_hi(x);
+          const float l = tc::tf32_lo(x, hi);
+          if (MODE == TC_UPDATE) lrow[ks * 64] = l;
+          dst[ks * tg] = hi;
+          dst[ks * tg + tlo] = l;
+        }
       }
     }
     tc::fence_async_smem();
@@ -233,9 +246,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc(const __grid_constant__ CUten
         tc::mma_commit(&bars[2]);
       }
       if (run1) p1_out = true;
-      ok = !run1 || tc::bar_wait(&bars[2], ph1);
+      ok = !run1 || tid != 0 || tc::bar_wait(&bars[2], ph1);
       if (!__syncthreads_and(ok)) { aborted = true; break; }
-      if (run1) { p1_out = false; ph1 ^= 1; }
+      if (run1) { tc::bar_test(&bars[2], ph1); p1_out = false; ph1 ^= 1; }
       tc::fence_after_sync();
       const int r = r_own;
       const int row = tile * TC_TR + r;
@@ -325,9 +338,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc(const __grid_constant__ CUten
   }
 
   if (!aborted && p2_out) {
-    const bool ok = tc::bar_wait(&bars[3], ph2);
+    const bool ok = tid != 0 || tc::bar_wait(&bars[3], ph2);
     if (!__syncthreads_and(ok)) aborted = true;
-    else { p2_out = false; ph2 ^= 1; }
+    else { tc::bar_test(&bars[3], ph2); p2_out = false; ph2 ^= 1; }
   }
   if (aborted) {
     if (tid == 0) atomicExch(a.status, USBS_ETIMEOUT);
@@ -392,6 +405,7 @@ void set_smem_attr() {
   static std::once_flag once;
   std::call_once(once, [] {
     cudaFuncSetAttribute(k_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_tc<MODE>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   });
 }
 
