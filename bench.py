@@ -306,6 +306,12 @@ def run_ours(args, world, rank, local, pg):
                    "obj_gap": r3["obj_gap"], "certifications": r3["certifications"],
                    "objective": r3["last"]["objective"], "dual_bound": r3["last"]["dual_bound"],
                    "relinf": r3["last"]["relinf"], "max_iters": args.obj_max_iters}
+    # C5 serving (bounded): served (continuous batching, warm starts) against plain FP64
+    serve = None
+    if args.serve_requests > 0:
+        from paper_2312_11801_gb300 import instances as I
+        serve = serve_measure(U, I, args.serve_requests, args.n_lo, args.n_hi, args.rho, 32,
+                              args.serve_max_iters, args.slots, args.load, seed=rank)
     hbm, peak_src = peaks()
     # roofline of the dominant bulk kernel (largest device time among the kinds with
     # algorithmic bytes; the k-sized one-CTA kernels are latency-bound, not HBM-bound)
@@ -335,6 +341,7 @@ def run_ours(args, world, rank, local, pg):
                    "timing": "profiling off in the timed region; kernel figures from "
                              f"{max(args.profile_steps, 1)} further solves with per-launch CUDA events"},
         "objective_relative": obj_rel,
+        "serve": serve,
         "e2e": {"value": world * args.e2e_steps / e2e_elapsed, "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
@@ -465,45 +472,39 @@ def serve_requests(I, count, n_lo, n_hi, seed=0):
     return reqs
 
 
-def run_serve(args, world, rank, local, pg):
-    """C5: a Poisson stream of MaxCut requests served by continuous batching (mixed
-    precision, warm starts from resident parents) against the plain path (FP64, one at a
-    time, cold).  Both see the same arrival times; the plain path's latencies follow
-    from its measured service times by a FIFO single-server queue."""
-    import torch
-    from paper_2312_11801_gb300 import build as B
-    B.build()
-    from paper_2312_11801_gb300 import usbs as U
-    from paper_2312_11801_gb300 import instances as I
-    torch.cuda.set_device(local)
-    reqs = serve_requests(I, args.requests, args.n_lo, args.n_hi, seed=rank)
-    # plain service times (sequential, FP64, cold) on this GPU
+def serve_measure(U, I, requests, n_lo, n_hi, rho, basis, max_iters, slots, load, seed=0):
+    """C5 serving: a Poisson stream of MaxCut requests (random geometric graphs, n
+    log-uniform on [n_lo, n_hi], every second request a 1 %-grown copy of an earlier one)
+    served by continuous batching (mixed precision, grown requests warm-started from their
+    resident parents) against the plain path (FP64, one request at a time, cold).  Both arms
+    see the same arrival times, at `load` times the plain path's measured capacity; the plain
+    arm's latencies follow from its measured service times by a FIFO single-server queue.
+    Solves/sec count converged requests over the makespan; p50/p99 are given over the
+    converged requests and over all of them."""
+    reqs = serve_requests(I, requests, n_lo, n_hi, seed=seed)
     plain_s = []
     for q in reqs:
         t0 = time.perf_counter()
-        with U.usbs_create(q["prob"], precision=U.PRECISION_FP64, rho=args.rho,
-                           max_iters=args.max_iters, lanczos_basis=args.lanczos_basis) as c:
+        with U.usbs_create(q["prob"], precision=U.PRECISION_FP64, rho=rho, max_iters=max_iters,
+                           lanczos_basis=basis) as c:
             r = U.usbs_solve(c, tol=TOL)
-        plain_s.append((time.perf_counter() - t0, r["converged"]))
-    plain_cap = len(reqs) / sum(s for s, _ in plain_s)
-    rate = args.load * plain_cap
-    rng = np.random.Generator(np.random.PCG64(99 + rank))
+        plain_s.append((time.perf_counter() - t0, bool(r["converged"])))
+    plain_cap = len(reqs) / sum(t for t, _ in plain_s)
+    rate = load * plain_cap
+    rng = np.random.Generator(np.random.PCG64(99 + seed))
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))
-    # plain latencies: FIFO queue with the same arrivals
     free_at, plain_lat = 0.0, []
-    for a, (s, _) in zip(arrivals, plain_s):
-        start = max(a, free_at)
-        free_at = start + s
-        plain_lat.append(free_at - a)
+    for a_t, (sv, _) in zip(arrivals, plain_s):
+        start = max(a_t, free_at)
+        free_at = start + sv
+        plain_lat.append(free_at - a_t)
     plain_makespan = free_at - arrivals[0]
-    # served: submit in real time
-    srv = U.usbs_server_create(max_slots=args.slots, cache_entries=args.requests,
-                               solver={"rho": args.rho, "lanczos_basis": args.lanczos_basis,
-                                       "max_iters": args.max_iters})
+    srv = U.usbs_server_create(max_slots=slots, cache_entries=requests,
+                               solver={"rho": rho, "lanczos_basis": basis, "max_iters": max_iters})
     done = []
     t0 = time.perf_counter()
-    for q, a in zip(reqs, arrivals):
-        while time.perf_counter() - t0 < a:
+    for q, a_t in zip(reqs, arrivals):
+        while time.perf_counter() - t0 < a_t:
             done += U.usbs_server_poll(srv, 64, wait_ms=1)
         U.usbs_server_submit(srv, q["id"], q["prob"], parent_id=q["parent"], tol=TOL)
     while len(done) < len(reqs):
@@ -511,25 +512,44 @@ def run_serve(args, world, rank, local, pg):
     st = U.usbs_server_get_stats(srv)
     srv.close()
     lat = [c["t_finish"] - c["t_arrival"] for c in done]
-    conv = sum(c["status"] == U.USBS_OK for c in done)
+    lat_conv = [c["t_finish"] - c["t_arrival"] for c in done if c["status"] == U.USBS_OK]
+    conv = len(lat_conv)
     served_makespan = max(c["t_finish"] for c in done) - min(c["t_arrival"] for c in done)
-    line = {
-        "metric": METRIC, "value": conv / served_makespan, "unit": UNIT, "n_gpus": world,
-        "steps": 1, "warmup": 0, "ms_per_step": 1e3 * served_makespan, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"serve_rgg_poisson_{args.requests}req_n{args.n_lo}-{args.n_hi}",
-                   "requests": len(reqs), "grown_from_parent": sum(q["parent"] >= 0 for q in reqs),
-                   "rho": args.rho, "tol": TOL, "load_vs_plain_capacity": args.load,
-                   "lanczos_basis": args.lanczos_basis, "max_iters": args.max_iters,
-                   "arrival_rate_per_s": rate, "slots": args.slots},
+    plain_conv_lat = [l for l, (_, ok) in zip(plain_lat, plain_s) if ok]
+    return {
+        "workload": f"serve_rgg_poisson_{requests}req_n{n_lo}-{n_hi}_grown50",
+        "requests": len(reqs), "grown_from_parent": sum(q["parent"] >= 0 for q in reqs),
+        "n_range": [min(q["prob"].n for q in reqs), max(q["prob"].n for q in reqs)],
+        "rho": rho, "tol": TOL, "lanczos_basis": basis, "max_iters": max_iters, "slots": slots,
+        "load_vs_plain_capacity": load, "arrival_rate_per_s": rate,
         "served": {"solves_per_s": conv / served_makespan, "converged": conv,
-                   "p50_s": _pct(lat, 50), "p99_s": _pct(lat, 99),
+                   "p50_s_converged": _pct(lat_conv, 50), "p99_s_converged": _pct(lat_conv, 99),
+                   "p50_s_all": _pct(lat, 50), "p99_s_all": _pct(lat, 99),
                    "warm": sum(c["warm"] for c in done), "peak_running": st["peak_running"],
-                   "peak_bytes": st["peak_bytes"]},
-        "plain_fp64": {"solves_per_s": sum(c for _, c in plain_s) / plain_makespan,
-                       "converged": sum(c for _, c in plain_s),
-                       "p50_s": _pct(plain_lat, 50), "p99_s": _pct(plain_lat, 99),
-                       "capacity_solves_per_s": plain_cap},
+                   "peak_bytes": st["peak_bytes"], "makespan_s": served_makespan},
+        "plain_fp64": {"solves_per_s": len(plain_conv_lat) / plain_makespan, "converged": len(plain_conv_lat),
+                       "p50_s_converged": _pct(plain_conv_lat, 50), "p99_s_converged": _pct(plain_conv_lat, 99),
+                       "p50_s_all": _pct(plain_lat, 50), "p99_s_all": _pct(plain_lat, 99),
+                       "capacity_solves_per_s": plain_cap, "makespan_s": plain_makespan},
+    }
+
+
+def run_serve(args, world, rank, local, pg):
+    """C5 as its own line (see serve_measure)."""
+    import torch
+    from paper_2312_11801_gb300 import build as B
+    B.build()
+    from paper_2312_11801_gb300 import usbs as U
+    from paper_2312_11801_gb300 import instances as I
+    torch.cuda.set_device(local)
+    sv = serve_measure(U, I, args.requests, args.n_lo, args.n_hi, args.rho, args.lanczos_basis,
+                       args.max_iters, args.slots, args.load, seed=rank)
+    line = {
+        "metric": METRIC, "value": sv["served"]["solves_per_s"], "unit": UNIT, "n_gpus": world,
+        "steps": 1, "warmup": 0, "ms_per_step": 1e3 * sv["served"]["makespan_s"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {k: v for k, v in sv.items() if k not in ("served", "plain_fp64")},
+        "served": sv["served"], "plain_fp64": sv["plain_fp64"],
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -645,6 +665,47 @@ def run_c3(args, world, rank, local, pg):
         print(json.dumps(line), flush=True)
 
 
+def run_sweep(args, world, rank, local, pg):
+    """k_c / k_p grid (the paper's App. F parameter sweeps, on synthetic graphs): cold-start
+    solves to both gates <= 1e-3 in mixed precision, one per (graph, k_c, k_p), and for one
+    setting the model value by the App. B.1 IPM against its closed form.  Reports iterations,
+    seconds and the objective of each."""
+    import torch
+    from paper_2312_11801_gb300 import build as B
+    B.build()
+    from paper_2312_11801_gb300 import usbs as U
+    from paper_2312_11801_gb300 import instances as I
+    torch.cuda.set_device(local)
+    graphs = {"er2000_d6": I.maxcut_er(2000, 6.0, 7), "rgg1000_d10": I.maxcut_rgg(1000, 10.0, seed=7)}
+    grid = [(8, 0), (7, 1), (6, 2), (5, 3), (4, 0), (4, 2), (2, 1)]
+    rows = []
+    t_all = time.perf_counter()
+    for gname, prob in graphs.items():
+        for (kc, kp) in grid:
+            for mv in ((0, 1) if (kc, kp) == (6, 2) else (0,)):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                with U.usbs_create(prob, precision=U.PRECISION_MIXED, k_c=kc, k_p=kp, rho=args.rho,
+                                   max_iters=min(args.max_iters, 1500), model_value_ipm=mv) as c:
+                    r = U.usbs_solve(c, tol=TOL)
+                torch.cuda.synchronize()
+                rows.append({"graph": gname, "k_c": kc, "k_p": kp, "model_value": "ipm" if mv else "closed",
+                             "iters": r["iters"], "converged": bool(r["converged"]),
+                             "seconds": time.perf_counter() - t0, "objective": r["last"]["objective"],
+                             "relgap": r["last"]["relgap"], "relinf": r["last"]["relinf"]})
+    elapsed = max_over_ranks(pg, time.perf_counter() - t_all)
+    conv = sum(r["converged"] for r in rows)
+    line = {
+        "metric": METRIC, "value": conv / elapsed, "unit": UNIT, "n_gpus": world, "steps": 1, "warmup": 0,
+        "ms_per_step": 1e3 * elapsed, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "kc_kp_sweep_er2000_rgg1000_mixed", "max_iters": min(args.max_iters, 1500), "rho": args.rho, "tol": TOL,
+                   "grid": grid, "solves": rows},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_reference(args, world, rank):
     """The oracle arm: each step is the bounded oracle sample of run_ours's workload."""
     if rank != 0:
@@ -695,7 +756,7 @@ def main():
     ap.add_argument("--obj-gap", type=float, default=1e-2,
                     help="objective-relative gap of the extra time-to-solution figure; 0 = skip it")
     ap.add_argument("--obj-max-iters", type=int, default=1500)
-    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "batched", "serve"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "batched", "serve", "sweep"])
     ap.add_argument("--c3-n", type=int, default=65536)
     ap.add_argument("--c3-rho", type=float, default=0.01)
     ap.add_argument("--rho", type=float, default=0.1, help="rho of the batched and served workloads")
@@ -703,6 +764,9 @@ def main():
     ap.add_argument("--plain-budget", type=float, default=60.0)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--requests", type=int, default=24)
+    ap.add_argument("--serve-requests", type=int, default=16,
+                    help="requests of the C5 serving figure added to the default line; 0 = skip it")
+    ap.add_argument("--serve-max-iters", type=int, default=400)
     ap.add_argument("--n-lo", type=int, default=1000)
     ap.add_argument("--n-hi", type=int, default=200000)
     ap.add_argument("--slots", type=int, default=8)
@@ -723,6 +787,8 @@ def main():
         run_batched(args, world, rank, local, pg)
     elif args.workload == "serve":
         run_serve(args, world, rank, local, pg)
+    elif args.workload == "sweep":
+        run_sweep(args, world, rank, local, pg)
     else:
         run_ours(args, world, rank, local, pg)
     if pg is not None:

@@ -34,8 +34,9 @@
 extern "C" {
 #endif
 
-#define USBS_ABI_VERSION 3   /* 2: usbs_eig_info.reruns, usbs_nystrom_round;
-                                3: certification of f(y) and the objective-relative gate */
+#define USBS_ABI_VERSION 4   /* 2: usbs_eig_info.reruns, usbs_nystrom_round;
+                                3: certification of f(y) and the objective-relative gate;
+                                4: the App. B.1 model-value IPM, usbs_selftest_tile_wait */
 
 /* status codes */
 #define USBS_OK          0
@@ -90,6 +91,11 @@ typedef struct usbs_params {
   /* When > 0, convergence also needs |f(y) - <C,X>| / |<C,X>| <= obj_gap_tol: the gap
    * relative to the objective itself, beside the paper's 1 + |<C,X>| denominator. */
   double obj_gap_tol;
+  /* 1 = compute the model value f^_t(y~) of the descent test (Sec. 3) by the interior
+   * point method of App. B.1 (a linear SDP over the model set) instead of its closed form
+   * (the maximum over the vertices 0, alpha Xbar / tr Xbar and alpha v v^T, v in range V);
+   * usbs_step_info carries both.  0 = closed form (the default). */
+  int    model_value_ipm;
 } usbs_params;
 
 typedef struct usbs_eig_info {
@@ -121,6 +127,8 @@ typedef struct usbs_step_info {
   double relinf_max;       /* ||A X - proj_K(A X)||_inf, scaled */
   double objective;        /* <C, X_{t+1}> in the units of the given problem */
   double dual_bound;       /* f(y_{t+1}) in the units of the given problem */
+  double f_hat_closed;     /* the closed-form model value (equals f_hat unless model_value_ipm) */
+  int    ipm_iters_b1;     /* Newton steps of the App. B.1 IPM (model_value_ipm = 1) */
 } usbs_step_info;
 
 typedef struct usbs_result {
@@ -227,6 +235,23 @@ int usbs_get_sketch(usbs_ctx* ctx, float* P, float* Psi, double* scalars);
  */
 int usbs_nystrom_round(usbs_ctx* ctx, double* lam, double* U, double* values, int* best, int8_t* signs);
 
+/*
+ * usbs_qap_round -- QAP rounding of the sketch (App. E, QAP: Rounding) for a problem built as
+ * the QAP relaxation of eq. qap_sdp, whose primal is indexed by [1; vec(Pi)] (n = nq^2 + 1,
+ * vec stacking columns).  From U of usbs_nystrom_round, every column u_k is oriented so that
+ * its first entry is non-negative, that entry is dropped, the rest is reshaped column by
+ * column into M_k (nq x nq), and the permutation Pi_k maximising <M_k, Pi_k> is found by the
+ * Hungarian method on the device; its cost is tr(W Pi_k D Pi_k^T).
+ *   W, D   : nq x nq FP64 host, row-major (flows and distances).
+ *   costs  : r FP64 host, the cost of every column's permutation (required).
+ *   scores : r FP64 host, <M_k, Pi_k>; may be NULL.
+ *   perms  : r x nq int host, perms[k nq + i] = the column j with Pi_k(i, j) = 1; may be NULL.
+ *   best   : host int, the column of least cost (smallest index on ties); may be NULL.
+ * Errors: USBS_EINVAL if n != nq^2 + 1, nq > 64 or r = 0; those of usbs_nystrom_round.
+ */
+int usbs_qap_round(usbs_ctx* ctx, int nq, const double* W, const double* D, double* costs,
+                   double* scores, int* perms, int* best);
+
 /* Current dual iterate y_t (m FP64 host), problem units. */
 int usbs_get_dual(usbs_ctx* ctx, double* y);
 
@@ -309,6 +334,19 @@ int usbs_kernel_stats(usbs_ctx* ctx, int kind, double* total_ms, long long* laun
                       double* bytes);
 /* Kernels this context has launched since usbs_create (profiling on or off). */
 long long usbs_launch_count(const usbs_ctx* ctx);
+
+/*
+ * usbs_selftest_tile_wait -- runs the bounded wait of the staged Gram-Schmidt tiles alone
+ * (one CTA on the current device; no context).  Every wait of a tile kernel on its staged
+ * copies polls at most 2^20 times with a short sleep (about 0.1 s); when it runs out the
+ * kernel writes USBS_ETIMEOUT to the Lanczos status word, waits (bounded again) for copies
+ * still in flight, releases its barriers and returns, so the device stays usable and the
+ * eigen solve returns USBS_ETIMEOUT.  deliver = 0 arms the barrier for a copy that is never
+ * issued, so the wait must run out: returns USBS_ETIMEOUT.  deliver = 1 issues the copy:
+ * returns USBS_OK.  USBS_ENOMEM / USBS_ECUDA on a failed allocation or launch.  The paper has
+ * no counterpart: this checks the failure path of the library's own waits without a fault.
+ */
+int usbs_selftest_tile_wait(int deliver);
 
 /*
  * usbs_sketch_update_static -- the sketch update of usbs_op_sketch_update,

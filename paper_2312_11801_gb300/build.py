@@ -15,7 +15,7 @@ BUILD = os.path.join(PKG, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libusbs.so")
 SOURCES = ["bulk.cu", "orth.cu", "small.cu", "engine.cu", "server.cu", "batch.cu",
-           "batch_f32_j32.cu", "batch_f32_j64.cu", "batch_f64_j32.cu", "noalloc.cu", "nystrom.cu", "tc_orth.cu"]
+           "batch_f32_j32.cu", "batch_f32_j64.cu", "batch_f64_j32.cu", "noalloc.cu", "nystrom.cu", "tc_orth.cu", "qap.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", INCLUDE, "-I", CSRC]

@@ -8,21 +8,24 @@
 
 namespace usbs {
 
-int batch_launch_f32_j32(const std::vector<Ctx*>& cs, cudaStream_t st, double tol, std::string& err);
-int batch_launch_f32_j64(const std::vector<Ctx*>& cs, cudaStream_t st, double tol, std::string& err);
-int batch_launch_f64_j32(const std::vector<Ctx*>& cs, cudaStream_t st, double tol, std::string& err);
+int batch_launch_f32_j32(const std::vector<Ctx*>& cs, cudaStream_t st, double tol, std::string& err, int bucket);
+int batch_launch_f32_j64(const std::vector<Ctx*>& cs, cudaStream_t st, double tol, std::string& err, int bucket);
+int batch_launch_f64_j32(const std::vector<Ctx*>& cs, cudaStream_t st, double tol, std::string& err, int bucket);
 
 // Eligible for the batched kernel: a basis the kernel is instantiated for (J = 32 in
 // both precisions, J = 64 in mixed precision) and no per-step host work (debug checks,
 // event profiling).
 bool batch_eligible(const Ctx* c) {
-  // the per-step path alone carries past information, certification and the
-  // objective-relative gate
-  if (c->debug || c->prof || c->kp > 0 || c->prm.certify_restarts > 0 || c->prm.obj_gap_tol > 0.0)
+  // the per-step path alone carries past information, certification, the
+  // objective-relative gate and the App. B.1 model-value IPM
+  if (c->debug || c->prof || c->kp > 0 || c->prm.certify_restarts > 0 || c->prm.obj_gap_tol > 0.0 ||
+      c->prm.model_value_ipm)
     return false;
   if (c->fp64) return c->J == 32;
   return c->J == 32 || c->J == 64;
 }
+
+int batch_bucket(int64_t n) { return n < 256 ? 0 : n < 512 ? 1 : n < 1024 ? 2 : n < 2048 ? 3 : 4; }
 
 int batch_run(const std::vector<Ctx*>& cs, cudaStream_t st, double tol, std::string& err) {
   if (cs.empty()) return USBS_OK;
@@ -33,9 +36,10 @@ int batch_run(const std::vector<Ctx*>& cs, cudaStream_t st, double tol, std::str
       err = "a batch must share precision and an instantiated Lanczos basis";
       return USBS_EINVAL;
     }
-  if (fp64) return batch_launch_f64_j32(cs, st, tol, err);
-  if (J == 32) return batch_launch_f32_j32(cs, st, tol, err);
-  return batch_launch_f32_j64(cs, st, tol, err);
+  const int bucket = batch_bucket(cs[0]->n);
+  if (fp64) return batch_launch_f64_j32(cs, st, tol, err, bucket);
+  if (J == 32) return batch_launch_f32_j32(cs, st, tol, err, bucket);
+  return batch_launch_f32_j64(cs, st, tol, err, bucket);
 }
 
 }  // namespace usbs

@@ -3,7 +3,7 @@
 #include "batch_kernel.cuh"
 
 namespace usbs {
-int batch_launch_f32_j32(const std::vector<Ctx*>& cs, cudaStream_t st, double tol, std::string& err) {
-  return launch_batch<float, float, 32>(cs, st, tol, err);
+int batch_launch_f32_j32(const std::vector<Ctx*>& cs, cudaStream_t st, double tol, std::string& err, int bucket) {
+  return launch_batch<float, float, 32>(cs, st, tol, err, bucket);
 }
 }  // namespace usbs

@@ -276,72 +276,150 @@ size_t batch_smem(int J) {
   m = std::max(m, sizeof(T) * (2 * (size_t)(nbmax + 1) * BlockStride<T>::value + 8 * 64 + 64));  // tiles
   m = std::max(m, sizeof(double) * 8 * 576);                                      // epilogues
   m = std::max(m, tc_red_bytes(5));                                               // FP32 update
-  m = std::max(m, sizeof(T) * (2 * (size_t)nbmax * BlockStride<T>::value + (size_t)J * (J / 2)));  // restart
+  m = std::max(m, sizeof(T) * (2 * (size_t)nbmax * BlockStride<T>::value) + 8 * (size_t)J * (J / 2));  // restart
   m = std::max(m, sizeof(T) * (4 * (size_t)J * (J + 1) + (size_t)J * J / 2));       // Ritz
   m = std::max(m, sizeof(T) * 128 * AUG + sizeof(double) * 4 * 880);              // gstats
   return m;
 }
 
-template <typename T, typename S, int J>
-int launch_batch(const std::vector<Ctx*>& cs, cudaStream_t st, double tol, std::string& err) {
-  const int count = (int)cs.size();
-  std::vector<BatchDesc> h(count);
-  for (int i = 0; i < count; ++i) {
-    const Ctx* c = cs[i];
-    BatchDesc& d = h[i];
-    std::memset(&d, 0, sizeof(d));
-    d.n = (int)c->n; d.m = (int)c->m; d.nnz_off = c->nnz_off; d.kc = c->kc; d.r = c->r;
-    d.J = c->J; d.keep = c->keep; d.has_offdiag_A = c->has_offdiag_A; d.any_ineq = c->any_ineq;
-    d.restarts = c->prm.lanczos_restarts; d.max_alt = c->prm.max_alt;
-    d.ipm_max_iter = c->prm.ipm_max_iter; d.max_iters = c->prm.max_iters;
-    d.tol = tol;
-    d.alpha = c->alpha; d.rho = c->prm.rho; d.beta = c->prm.beta; d.bnorm = c->bnorm;
-    d.lanczos_tol = c->prm.lanczos_tol; d.ipm_mu_tol = c->prm.ipm_mu_tol; d.alt_tol = c->prm.alt_tol;
-    d.seed = c->seed; d.rng_counter = c->rng_counter;
-    d.rowptr = c->rowptr; d.col = c->col; d.valC64 = c->valC64; d.valM = c->valM; d.valC = c->valC;
-    d.diagC64 = c->diagC64; d.dM = c->dM; d.dC = c->dC;
-    d.diag_ptr = c->diag_ptr; d.diag_con = c->diag_con; d.diag_val = c->diag_val;
-    d.slot_ptr = c->slot_ptr; d.slot_con = c->slot_con; d.slot_val = c->slot_val;
-    d.con_ptr = c->con_ptr; d.ent_i = c->ent_i; d.ent_j = c->ent_j; d.ent_v = c->ent_v;
-    d.b = c->b; d.ineq = c->ineq;
-    d.y = c->y; d.ycand = c->ycand; d.ax = c->ax; d.axnew = c->axnew; d.nu = c->nu;
-    d.V = c->V; d.Vnew = c->Vnew; d.W = c->W; d.Q = c->Q; d.Q2 = c->Q2; d.P = c->P; d.Psi = c->Psi;
-    d.sc = c->sc; d.lz = c->lz; d.red = c->red;
-  }
+// Per (instantiation, size bucket) launch plan: pinned and device descriptor arrays, the
+// work counter, and a CUDA graph of [descriptors up, counter reset, persistent kernel,
+// descriptors down] captured once and replayed while the bucket's instance count and grid
+// stay the same (the graph's copies read and write the plan's fixed buffers, so a replay
+// only needs the descriptors refreshed in the pinned array).
+struct BatchPlan {
+  std::mutex mu;
+  int count = 0, grid = 0;
+  BatchDesc* h = nullptr;     // pinned
   BatchDesc* dd = nullptr;
   int* dnext = nullptr;
-  auto fail = [&](cudaError_t e, const char* what) {
-    err = std::string(what) + ": " + cudaGetErrorString(e);
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  void release() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (h) cudaFreeHost(h);
     if (dd) cudaFree(dd);
     if (dnext) cudaFree(dnext);
+    exec = nullptr; graph = nullptr; h = nullptr; dd = nullptr; dnext = nullptr;
+    count = 0; grid = 0;
+  }
+};
+
+inline void fill_desc(BatchDesc& d, const Ctx* c, double tol, int max_iters) {
+  std::memset(&d, 0, sizeof(d));
+  d.n = (int)c->n; d.m = (int)c->m; d.nnz_off = c->nnz_off; d.kc = c->kc; d.r = c->r;
+  d.J = c->J; d.keep = c->keep; d.has_offdiag_A = c->has_offdiag_A; d.any_ineq = c->any_ineq;
+  d.restarts = c->prm.lanczos_restarts; d.max_alt = c->prm.max_alt;
+  d.ipm_max_iter = c->prm.ipm_max_iter; d.max_iters = max_iters;
+  d.tol = tol;
+  d.alpha = c->alpha; d.rho = c->prm.rho; d.beta = c->prm.beta; d.bnorm = c->bnorm;
+  d.lanczos_tol = c->prm.lanczos_tol; d.ipm_mu_tol = c->prm.ipm_mu_tol; d.alt_tol = c->prm.alt_tol;
+  d.seed = c->seed; d.rng_counter = c->rng_counter;
+  d.rowptr = c->rowptr; d.col = c->col; d.valC64 = c->valC64; d.valM = c->valM; d.valC = c->valC;
+  d.diagC64 = c->diagC64; d.dM = c->dM; d.dC = c->dC;
+  d.diag_ptr = c->diag_ptr; d.diag_con = c->diag_con; d.diag_val = c->diag_val;
+  d.slot_ptr = c->slot_ptr; d.slot_con = c->slot_con; d.slot_val = c->slot_val;
+  d.con_ptr = c->con_ptr; d.ent_i = c->ent_i; d.ent_j = c->ent_j; d.ent_v = c->ent_v;
+  d.b = c->b; d.ineq = c->ineq;
+  d.y = c->y; d.ycand = c->ycand; d.ax = c->ax; d.axnew = c->axnew; d.nu = c->nu;
+  d.V = c->V; d.Vnew = c->Vnew; d.W = c->W; d.Q = c->Q; d.Q2 = c->Q2; d.P = c->P; d.Psi = c->Psi;
+  d.sc = c->sc; d.lz = c->lz; d.red = c->red;
+}
+
+// Cold-start solves of cs (one size bucket of one instantiation) on stream st.  The
+// instances go to the CTAs largest first (the atomic counter hands them out in order), and
+// the grid (resident CTAs per SM, 1, 2 or the occupancy maximum) is chosen per bucket by a
+// timed probe on the first call: each candidate runs the bucket's cold starts and three
+// iterations, the fastest wins and is kept for the process.  A probe changes no context:
+// its results are not copied back, and the real solve starts cold.
+template <typename T, typename S, int J>
+int launch_batch(const std::vector<Ctx*>& cs_in, cudaStream_t st, double tol, std::string& err, int bucket) {
+  std::vector<Ctx*> cs(cs_in);
+  std::stable_sort(cs.begin(), cs.end(), [](const Ctx* a, const Ctx* b) {
+    return a->n * (int64_t)(a->nnz_off + a->n) > b->n * (int64_t)(b->nnz_off + b->n);
+  });
+  const int count = (int)cs.size();
+  static std::mutex plans_mu;
+  static BatchPlan plans[8];
+  static int tuned_per_sm[8] = {};
+  const int bk = std::max(0, std::min(bucket, 7));
+  BatchPlan& P = plans[bk];
+  std::lock_guard<std::mutex> plan_lock(P.mu);
+  cudaError_t e;
+  auto fail = [&](cudaError_t ee, const char* what) {
+    err = std::string(what) + ": " + cudaGetErrorString(ee);
+    cudaGetLastError();
+    P.release();
     return USBS_ECUDA;
   };
-  cudaError_t e;
-  if ((e = cudaMalloc(&dd, sizeof(BatchDesc) * count))) return fail(e, "cudaMalloc");
-  if ((e = cudaMalloc(&dnext, sizeof(int)))) return fail(e, "cudaMalloc");
-  if ((e = cudaMemcpyAsync(dd, h.data(), sizeof(BatchDesc) * count, cudaMemcpyHostToDevice, st)))
-    return fail(e, "descriptor upload");
-  if ((e = cudaMemsetAsync(dnext, 0, sizeof(int), st))) return fail(e, "cudaMemsetAsync");
   const size_t smem = batch_smem<T>(J);
   static std::once_flag once;
   std::call_once(once, [&] {
-    cudaFuncSetAttribute(k_batch_solve<T, S, J>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
+    cudaFuncSetAttribute(k_batch_solve<T, S, J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   });
-  int per_sm = 0;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_solve<T, S, J>, BT, smem)))
+  int max_per_sm = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&max_per_sm, k_batch_solve<T, S, J>, BT, smem)))
     return fail(e, "occupancy");
+  max_per_sm = std::max(max_per_sm, 1);
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = std::max(1, std::min(count, std::max(per_sm, 1) * sms));
-  k_batch_solve<T, S, J><<<grid, BT, smem, st>>>(dd, count, dnext);
-  if ((e = cudaGetLastError())) return fail(e, "k_batch_solve launch");
-  if ((e = cudaMemcpyAsync(h.data(), dd, sizeof(BatchDesc) * count, cudaMemcpyDeviceToHost, st)))
-    return fail(e, "descriptor download");
+  if (P.count != count) {
+    P.release();
+    if ((e = cudaMallocHost(reinterpret_cast<void**>(&P.h), sizeof(BatchDesc) * count))) return fail(e, "cudaMallocHost");
+    if ((e = cudaMalloc(&P.dd, sizeof(BatchDesc) * count))) return fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&P.dnext, sizeof(int)))) return fail(e, "cudaMalloc");
+    P.count = count;
+  }
+  // autotune the grid of this bucket once
+  int per_sm;
+  {
+    std::lock_guard<std::mutex> lk(plans_mu);
+    per_sm = tuned_per_sm[bk];
+  }
+  if (per_sm == 0) {
+    const int cands[3] = {1, std::min(2, max_per_sm), max_per_sm};
+    float best_ms = 0.f;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int ci = 0; ci < 3; ++ci) {
+      if (ci > 0 && cands[ci] == cands[ci - 1]) continue;
+      const int grid = std::max(1, std::min(count, cands[ci] * sms));
+      for (int i = 0; i < count; ++i) fill_desc(P.h[i], cs[i], tol, std::min(3, cs[i]->prm.max_iters));
+      if ((e = cudaMemcpyAsync(P.dd, P.h, sizeof(BatchDesc) * count, cudaMemcpyHostToDevice, st))) return fail(e, "probe upload");
+      if ((e = cudaMemsetAsync(P.dnext, 0, sizeof(int), st))) return fail(e, "probe reset");
+      cudaEventRecord(e0, st);
+      k_batch_solve<T, S, J><<<grid, BT, smem, st>>>(P.dd, count, P.dnext);
+      cudaEventRecord(e1, st);
+      if ((e = cudaStreamSynchronize(st))) return fail(e, "probe");
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (per_sm == 0 || ms < best_ms) { best_ms = ms; per_sm = cands[ci]; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> lk(plans_mu);
+    tuned_per_sm[bk] = per_sm;
+  }
+  const int grid = std::max(1, std::min(count, per_sm * sms));
+  if (!P.exec || P.grid != grid) {
+    if (P.exec) { cudaGraphExecDestroy(P.exec); P.exec = nullptr; }
+    if (P.graph) { cudaGraphDestroy(P.graph); P.graph = nullptr; }
+    if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal))) return fail(e, "capture");
+    cudaMemcpyAsync(P.dd, P.h, sizeof(BatchDesc) * count, cudaMemcpyHostToDevice, st);
+    cudaMemsetAsync(P.dnext, 0, sizeof(int), st);
+    k_batch_solve<T, S, J><<<grid, BT, smem, st>>>(P.dd, count, P.dnext);
+    cudaMemcpyAsync(P.h, P.dd, sizeof(BatchDesc) * count, cudaMemcpyDeviceToHost, st);
+    if ((e = cudaStreamEndCapture(st, &P.graph))) return fail(e, "capture end");
+    if ((e = cudaGraphInstantiate(&P.exec, P.graph, 0))) return fail(e, "graph instantiate");
+    P.grid = grid;
+  }
+  for (int i = 0; i < count; ++i) fill_desc(P.h[i], cs[i], tol, cs[i]->prm.max_iters);
+  if ((e = cudaGraphLaunch(P.exec, st))) return fail(e, "graph launch");
   if ((e = cudaStreamSynchronize(st))) return fail(e, "k_batch_solve");
-  cudaFree(dd);
-  cudaFree(dnext);
+  const BatchDesc* h = P.h;
   for (int i = 0; i < count; ++i) {
     Ctx* c = cs[i];
     const BatchDesc& d = h[i];
@@ -352,17 +430,14 @@ int launch_batch(const std::vector<Ctx*>& cs, cudaStream_t st, double tol, std::
     c->rng_counter = d.rng_counter;
     c->total_matvecs += d.matvecs;
     c->started = d.status == USBS_OK;
-  }
-  // results are read back by the caller from each context
-  for (int i = 0; i < count; ++i) {
-    Ctx* c = cs[i];
-    c->batch_iters = h[i].iters;
-    c->batch_converged = h[i].converged;
-    c->batch_descent = h[i].descent_steps;
-    c->batch_status = h[i].status;
-    c->batch_matvecs = h[i].matvecs;
-    c->batch_last_matvecs = h[i].last_matvecs;
-    c->batch_n_alt = h[i].last_n_alt;
+    // results are read back by the caller from each context
+    c->batch_iters = d.iters;
+    c->batch_converged = d.converged;
+    c->batch_descent = d.descent_steps;
+    c->batch_status = d.status;
+    c->batch_matvecs = d.matvecs;
+    c->batch_last_matvecs = d.last_matvecs;
+    c->batch_n_alt = d.last_n_alt;
   }
   return USBS_OK;
 }

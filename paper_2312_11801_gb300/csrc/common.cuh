@@ -64,6 +64,9 @@ struct DevScalars {
   double cx_prev, tr_prev;   // Xbar_t's <C, Xbar>, tr Xbar before the step's update
   // past information (k_p > 0): S = S_p + S_c and the k_p leading eigenvectors Q_p of S
   double Sp[64], Sc[64], Qp[64];
+  // the model value by the App. B.1 IPM (model_value_ipm = 1) beside the closed form
+  double f_hat_ipm, f_hat_closed;
+  int ipm_iters_b1, pad2;
 };
 
 // ---- Lanczos device state -------------------------------------------------------------
@@ -192,7 +195,10 @@ struct Ctx {
 // A context the persistent batched kernel can solve (its basis size is instantiated and
 // no per-step host work is enabled).
 bool batch_eligible(const Ctx* c);
-// Cold-start solves of all contexts (same precision and basis) in one launch on stream st.
+// Size bucket of an instance for the batched solver (n < 256, 512, 1024, 2048, larger).
+int batch_bucket(int64_t n);
+// Cold-start solves of all contexts (same precision, basis and size bucket) in one launch of
+// the persistent kernel (a CUDA graph replayed per bucket) on stream st.
 int batch_run(const std::vector<Ctx*>& cs, cudaStream_t st, double tol, std::string& err);
 // usbs_result of a context's last batched solve, as usbs_solve would report it.
 int batch_result(Ctx* c, usbs_result* out);
@@ -320,6 +326,8 @@ void reduce_max_slot(Ctx* c, int nparts, int slot, double* out);
 void launch_chol_block(Ctx* c, int j, int nb, int write_T, int is_resid, int defl_pass);
 void launch_ritz(Ctx* c, int J, int keep, int spec);
 void launch_ipm(Ctx* c, int first_pass);
+// App. B.1: the model value at y~ by the IPM (model_value_ipm = 1), after k_xupdate's sums
+void launch_ipm_b1(Ctx* c);
 void launch_finish(Ctx* c);
 void launch_commit(Ctx* c);
 void launch_cold(Ctx* c);

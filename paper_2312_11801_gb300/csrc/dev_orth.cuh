@@ -149,6 +149,18 @@ __device__ __forceinline__ bool tile_wait(uint64_t* bar, unsigned parity, int* s
   return false;
 }
 
+// The same wait for a whole CTA: thread 0 polls while the others sleep in the barrier (so
+// the waiting warps take no issue slots from the other CTA on the SM); afterwards every
+// thread observes the completed phase once itself, which makes the copies' bytes visible to
+// it.  Every thread of the CTA must call it.
+__device__ __forceinline__ bool tile_wait_cta(uint64_t* bar, unsigned parity, int* status) {
+  bool ok = true;
+  if (threadIdx.x == 0) ok = tile_wait(bar, parity, status);
+  ok = __syncthreads_and(ok) != 0;
+  if (ok) mbar_test(bar, parity);
+  return ok;
+}
+
 // After the tile loop: on an abort, wait (bounded) for copies that may still be landing in
 // either stage, then release the barriers.
 __device__ __forceinline__ void tiles_end(uint64_t* bar, bool aborted, int it_abort, int left_after, int* status) {
@@ -199,15 +211,19 @@ __device__ __forceinline__ SplitB split_b(float b0, float b1) {
   tf32_split(b1, s.h1, s.l1);
   return s;
 }
-__device__ __forceinline__ void mma3(float (&d)[4], float a0, float a1, float a2, float a3, const SplitB& b) {
+// The two small terms go to ds, the large one to db: two accumulators, so that consecutive
+// MMAs of a tile do not wait on one another (an m16n8k8 MMA's result is ready only after its
+// full latency); the caller adds ds to db at the end.
+__device__ __forceinline__ void mma3s(float (&ds)[4], float (&db)[4], float a0, float a1, float a2, float a3,
+                                      const SplitB& b) {
   uint32_t h0, h1, h2, h3, l0, l1, l2, l3;
   tf32_split(a0, h0, l0);
   tf32_split(a1, h1, l1);
   tf32_split(a2, h2, l2);
   tf32_split(a3, h3, l3);
-  mma_tf32(d, l0, l1, l2, l3, b.h0, b.h1);
-  mma_tf32(d, h0, h1, h2, h3, b.l0, b.l1);
-  mma_tf32(d, h0, h1, h2, h3, b.h0, b.h1);
+  mma_tf32(ds, l0, l1, l2, l3, b.h0, b.h1);
+  mma_tf32(db, h0, h1, h2, h3, b.h0, b.h1);
+  mma_tf32(ds, h0, h1, h2, h3, b.l0, b.l1);
 }
 
 // shared memory of the warp reduction of tc_reduce_xty with MAXP pairs: 8 x MAXP x 32 x 4
@@ -224,7 +240,7 @@ __device__ __forceinline__ int dfrag_reg(int m, int c) { return ((m >> 3) << 1) 
 // k-steps w and w + 8 of the 128-row tile.
 template <int MAXP>
 __device__ __forceinline__ void tc_accum_xty(const float* st, int nblk, const float* Y, int warp, int g, int t,
-                                             float (&acc)[MAXP][4]) {
+                                             float (&accs)[MAXP][4], float (&accb)[MAXP][4]) {
   constexpr int BS = BlockStride<float>::value;
   const int off = t * 8 + g;   // element (row t, column g) of an 8-row step; + 32 for row t + 4
 #pragma unroll
@@ -239,7 +255,7 @@ __device__ __forceinline__ void tc_accum_xty(const float* st, int nblk, const fl
         const bool two = 2 * p + 1 < nblk;
         const float a0 = q0[0], a2 = q0[32];
         const float a1 = two ? q0[BS] : 0.f, a3 = two ? q0[BS + 32] : 0.f;
-        mma3(acc[p], a0, a1, a2, a3, b);
+        mma3s(accs[p], accb[p], a0, a1, a2, a3, b);
       }
     }
   }
@@ -275,11 +291,11 @@ __device__ __forceinline__ void tc_tproj(const int cta, const int ncta, int n, c
   float* stages = reinterpret_cast<float*>(smem_raw);
   const int sstride = (nb + 1) * BS;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  float acc[4][4];
+  float acc[4][4], accb[4][4];
 #pragma unroll
   for (int p = 0; p < 4; ++p)
 #pragma unroll
-    for (int u = 0; u < 4; ++u) acc[p][u] = 0.f;
+    for (int u = 0; u < 4; ++u) acc[p][u] = accb[p][u] = 0.f;
   const int ntiles = (n + TR - 1) / TR;
   int tile = cta;
   __shared__ uint64_t tbar[2];
@@ -290,18 +306,22 @@ __device__ __forceinline__ void tc_tproj(const int cta, const int ncta, int n, c
   for (int it = 0; tile < ntiles; ++it, tile += ncta) {
     const int next = tile + ncta;
     if (next < ntiles) tile_load<float, TR>(stages + ((it + 1) & 1) * sstride, Q, bstride, nb, W, n, next * TR, &tbar[(it + 1) & 1]);
-    if (!__syncthreads_and(tile_wait(&tbar[it & 1], (it >> 1) & 1, status))) {
+    if (!tile_wait_cta(&tbar[it & 1], (it >> 1) & 1, status)) {
       aborted = true;
       it_abort = it;
       left_after = next < ntiles;
       break;
     }
     const float* st = stages + (it & 1) * sstride;
-    tc_accum_xty<4>(st, nb, st + (size_t)nb * BS, warp, g, t, acc);
+    tc_accum_xty<4>(st, nb, st + (size_t)nb * BS, warp, g, t, acc, accb);
     __syncthreads();
   }
   tiles_end(tbar, aborted, it_abort, left_after, status);
   __syncthreads();
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[p][u] = accb[p][u] + acc[p][u];
   tc_reduce_xty<4>(acc, nb, warp, lane, reinterpret_cast<float*>(smem_raw), partials + (size_t)cta * PART_STRIDE,
                    [](int blk, int a, int c) { return blk * 64 + a * 8 + c; });
 }
@@ -323,11 +343,11 @@ __device__ __forceinline__ void tc_tupdate(const int cta, const int ncta, int n,
 #pragma unroll
   for (int b = 0; b < 8; ++b)
     hb[b] = (b < nb) ? split_b(Hs[b * 64 + t * 8 + g], Hs[b * 64 + (t + 4) * 8 + g]) : SplitB{0u, 0u, 0u, 0u};
-  float acc[5][4];
+  float acc[5][4], accb[5][4];
 #pragma unroll
   for (int p = 0; p < 5; ++p)
 #pragma unroll
-    for (int u = 0; u < 4; ++u) acc[p][u] = 0.f;
+    for (int u = 0; u < 4; ++u) acc[p][u] = accb[p][u] = 0.f;
   const int ntiles = (n + TR - 1) / TR;
   int tile = cta;
   __shared__ uint64_t tbar[2];
@@ -338,7 +358,7 @@ __device__ __forceinline__ void tc_tupdate(const int cta, const int ncta, int n,
   for (int it = 0; tile < ntiles; ++it, tile += ncta) {
     const int next = tile + ncta;
     if (next < ntiles) tile_load<float, TR>(stages + ((it + 1) & 1) * sstride, Q, bstride, nb, W, n, next * TR, &tbar[(it + 1) & 1]);
-    if (!__syncthreads_and(tile_wait(&tbar[it & 1], (it >> 1) & 1, status))) {
+    if (!tile_wait_cta(&tbar[it & 1], (it >> 1) & 1, status)) {
       aborted = true;
       it_abort = it;
       left_after = next < ntiles;
@@ -349,14 +369,19 @@ __device__ __forceinline__ void tc_tupdate(const int cta, const int ncta, int n,
     // phase 1: rows 16 warp .. 16 warp + 15 of X = W - Q H
     {
       const int rb = 16 * warp;
-      float d[4] = {0.f, 0.f, 0.f, 0.f};
+      // four accumulators (small / large terms of even / odd blocks): independent MMA chains
+      float d[4] = {0.f, 0.f, 0.f, 0.f}, e0[4] = {0.f, 0.f, 0.f, 0.f};
+      float s1[4] = {0.f, 0.f, 0.f, 0.f}, e1[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int b = 0; b < 8; ++b) {
         if (b < nb) {
           const float* q = st + (size_t)b * BS + (size_t)rb * 8;
-          mma3(d, q[g * 8 + t], q[(g + 8) * 8 + t], q[g * 8 + t + 4], q[(g + 8) * 8 + t + 4], hb[b]);
+          if (b & 1) mma3s(s1, e1, q[g * 8 + t], q[(g + 8) * 8 + t], q[g * 8 + t + 4], q[(g + 8) * 8 + t + 4], hb[b]);
+          else mma3s(d, e0, q[g * 8 + t], q[(g + 8) * 8 + t], q[g * 8 + t + 4], q[(g + 8) * 8 + t + 4], hb[b]);
         }
       }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) d[u] = (e0[u] + e1[u]) + (d[u] + s1[u]);
       float* x0 = Xs + (size_t)(rb + g) * 8 + 2 * t;
       float* x1 = Xs + (size_t)(rb + g + 8) * 8 + 2 * t;
       const float v0 = x0[0] - d[0], v1 = x0[1] - d[1], v2 = x1[0] - d[2], v3 = x1[1] - d[3];
@@ -367,11 +392,15 @@ __device__ __forceinline__ void tc_tupdate(const int cta, const int ncta, int n,
     }
     __syncthreads();
     // phase 2: H2 = Q^T X and G = X^T X (X is block nb of the pair list; rows past n are 0)
-    tc_accum_xty<5>(st, nb + 1, Xs, warp, g, t, acc);
+    tc_accum_xty<5>(st, nb + 1, Xs, warp, g, t, acc, accb);
     __syncthreads();
   }
   tiles_end(tbar, aborted, it_abort, left_after, status);
   __syncthreads();
+#pragma unroll
+  for (int p = 0; p < 5; ++p)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[p][u] = accb[p][u] + acc[p][u];
   tc_reduce_xty<5>(acc, nb + 1, warp, lane, reinterpret_cast<float*>(smem_raw), partials + (size_t)cta * PART_STRIDE,
                    [nb](int blk, int a, int c) { return (blk < nb ? blk * 64 : 512) + a * 8 + c; });
 }
@@ -408,7 +437,7 @@ __device__ __forceinline__ void tc_tfinalize(const int cta, const int ncta, int 
   for (int it = 0; tile < ntiles; ++it, tile += ncta) {
     const int next = tile + ncta;
     if (next < ntiles) tile_load<float, TR>(stages + ((it + 1) & 1) * sstride, Q, bstride, nb, W, n, next * TR, &tbar[(it + 1) & 1]);
-    if (!__syncthreads_and(tile_wait(&tbar[it & 1], (it >> 1) & 1, status))) {
+    if (!tile_wait_cta(&tbar[it & 1], (it >> 1) & 1, status)) {
       aborted = true;
       it_abort = it;
       left_after = next < ntiles;
@@ -417,22 +446,28 @@ __device__ __forceinline__ void tc_tfinalize(const int cta, const int ncta, int 
     float* st = stages + (it & 1) * sstride;
     float* Xs = st + (size_t)nb * BS;
     const int rb = 16 * warp;
-    float d[4] = {0.f, 0.f, 0.f, 0.f};
+    float d[4] = {0.f, 0.f, 0.f, 0.f}, e0[4] = {0.f, 0.f, 0.f, 0.f};
+    float s1[4] = {0.f, 0.f, 0.f, 0.f}, e1[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int b = 0; b < 8; ++b) {
       if (b < nb) {
         const float* q = st + (size_t)b * BS + (size_t)rb * 8;
-        mma3(d, q[g * 8 + t], q[(g + 8) * 8 + t], q[g * 8 + t + 4], q[(g + 8) * 8 + t + 4], hb[b]);
+        if (b & 1) mma3s(s1, e1, q[g * 8 + t], q[(g + 8) * 8 + t], q[g * 8 + t + 4], q[(g + 8) * 8 + t + 4], hb[b]);
+        else mma3s(d, e0, q[g * 8 + t], q[(g + 8) * 8 + t], q[g * 8 + t + 4], q[(g + 8) * 8 + t + 4], hb[b]);
       }
     }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) d[u] = (e0[u] + e1[u]) + (d[u] + s1[u]);
     // X = W - Q H2 back into this warp's own rows, then (X R^-1) as a second MMA
     float* x0 = Xs + (size_t)(rb + g) * 8 + 2 * t;
     float* x1 = Xs + (size_t)(rb + g + 8) * 8 + 2 * t;
     x0[0] -= d[0]; x0[1] -= d[1]; x1[0] -= d[2]; x1[1] -= d[3];
     __syncwarp();
     const float* xr = Xs + (size_t)rb * 8;
-    float o[4] = {0.f, 0.f, 0.f, 0.f};
-    mma3(o, xr[g * 8 + t], xr[(g + 8) * 8 + t], xr[g * 8 + t + 4], xr[(g + 8) * 8 + t + 4], rb0);
+    float o[4] = {0.f, 0.f, 0.f, 0.f}, ob[4] = {0.f, 0.f, 0.f, 0.f};
+    mma3s(o, ob, xr[g * 8 + t], xr[(g + 8) * 8 + t], xr[g * 8 + t + 4], xr[(g + 8) * 8 + t + 4], rb0);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) o[u] = ob[u] + o[u];
     const int row0 = tile * TR + rb + g, row1 = row0 + 8;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
@@ -448,7 +483,7 @@ __device__ __forceinline__ void tc_tfinalize(const int cta, const int ncta, int 
 }
 
 // out[o] = Q[:, :J] Y[:, 8o : 8o + 8] for o < nout <= 4; the residual block copied to
-// out[resid_slot] when resid is given.  Ys: J x 8 nout (FP32) in shared memory.
+// out[resid_slot] when resid is given.  Ys: J x 8 nout split pairs in shared memory.
 __device__ __forceinline__ void tc_trestart(const int cta, const int ncta, int n, const float* Q, size_t bstride,
                                             int nbk, int nout, const double* Y, float* out, size_t ostride,
                                             const float* resid, int resid_slot, int* status) {
@@ -456,10 +491,15 @@ __device__ __forceinline__ void tc_trestart(const int cta, const int ncta, int n
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* stages = reinterpret_cast<float*>(smem_raw);
   const int sstride = nbk * BS;
-  float* Ys = stages + 2 * sstride;
+  // Y split once per launch into TF32 high and low parts: (hi, lo) pairs, J x 8 nout
+  uint2* Ys = reinterpret_cast<uint2*>(stages + 2 * sstride);
   const int J = nbk * 8, ncol = nout * 8;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
-  for (int u = tid; u < J * ncol; u += blockDim.x) Ys[u] = (float)Y[(u / ncol) * JMAX + (u % ncol)];
+  for (int u = tid; u < J * ncol; u += blockDim.x) {
+    uint32_t hi, lo;
+    tf32_split((float)Y[(u / ncol) * JMAX + (u % ncol)], hi, lo);
+    Ys[u] = make_uint2(hi, lo);
+  }
   const int ntiles = (n + TR - 1) / TR;
   int tile = cta;
   __shared__ uint64_t tbar[2];
@@ -470,7 +510,7 @@ __device__ __forceinline__ void tc_trestart(const int cta, const int ncta, int n
   for (int it = 0; tile < ntiles; ++it, tile += ncta) {
     const int next = tile + ncta;
     if (next < ntiles) tile_load<float, TR>(stages + ((it + 1) & 1) * sstride, Q, bstride, nbk, nullptr, n, next * TR, &tbar[(it + 1) & 1]);
-    if (!__syncthreads_and(tile_wait(&tbar[it & 1], (it >> 1) & 1, status))) {
+    if (!tile_wait_cta(&tbar[it & 1], (it >> 1) & 1, status)) {
       aborted = true;
       it_abort = it;
       left_after = next < ntiles;
@@ -478,22 +518,33 @@ __device__ __forceinline__ void tc_trestart(const int cta, const int ncta, int n
     }
     const float* st = stages + (it & 1) * sstride;
     const int rb = 16 * warp;
-    float d[4][4];
+    // small terms in d, large terms in e: independent accumulators per output block
+    float d[4][4], e[4][4];
 #pragma unroll
     for (int o = 0; o < 4; ++o)
 #pragma unroll
-      for (int u = 0; u < 4; ++u) d[o][u] = 0.f;
+      for (int u = 0; u < 4; ++u) d[o][u] = e[o][u] = 0.f;
     for (int b = 0; b < nbk; ++b) {
       const float* q = st + (size_t)b * BS + (size_t)rb * 8;
-      const float a0 = q[g * 8 + t], a1 = q[(g + 8) * 8 + t], a2 = q[g * 8 + t + 4], a3 = q[(g + 8) * 8 + t + 4];
+      uint32_t h0, h1, h2, h3, l0, l1, l2, l3;
+      tf32_split(q[g * 8 + t], h0, l0);
+      tf32_split(q[(g + 8) * 8 + t], h1, l1);
+      tf32_split(q[g * 8 + t + 4], h2, l2);
+      tf32_split(q[(g + 8) * 8 + t + 4], h3, l3);
 #pragma unroll
       for (int o = 0; o < 4; ++o) {
         if (o < nout) {
-          const SplitB yb = split_b(Ys[(b * 8 + t) * ncol + 8 * o + g], Ys[(b * 8 + t + 4) * ncol + 8 * o + g]);
-          mma3(d[o], a0, a1, a2, a3, yb);
+          const uint2 y0 = Ys[(b * 8 + t) * ncol + 8 * o + g], y1 = Ys[(b * 8 + t + 4) * ncol + 8 * o + g];
+          mma_tf32(d[o], l0, l1, l2, l3, y0.x, y1.x);
+          mma_tf32(e[o], h0, h1, h2, h3, y0.x, y1.x);
+          mma_tf32(d[o], h0, h1, h2, h3, y0.y, y1.y);
         }
       }
     }
+#pragma unroll
+    for (int o = 0; o < 4; ++o)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) d[o][u] = e[o][u] + d[o][u];
     const int row0 = tile * TR + rb + g, row1 = row0 + 8;
 #pragma unroll
     for (int o = 0; o < 4; ++o) {
@@ -579,7 +630,7 @@ __device__ __forceinline__ void k_tproj_dev(const int cta, const int ncta, int n
   for (int it = 0; tile < ntiles; ++it, tile += ncta) {
     const int next = tile + ncta;
     if (next < ntiles) tile_load<T, TR>(stages + ((it + 1) & 1) * sstride, Q, bstride, nb, W, n, next * TR, &tbar[(it + 1) & 1]);
-    if (!__syncthreads_and(tile_wait(&tbar[it & 1], (it >> 1) & 1, status))) {
+    if (!tile_wait_cta(&tbar[it & 1], (it >> 1) & 1, status)) {
       aborted = true;
       it_abort = it;
       left_after = next < ntiles;
@@ -646,7 +697,7 @@ __device__ __forceinline__ void k_tupdate_dev(const int cta, const int ncta, int
   for (int it = 0; tile < ntiles; ++it, tile += ncta) {
     const int next = tile + ncta;
     if (next < ntiles) tile_load<T, TR>(stages + ((it + 1) & 1) * sstride, Q, bstride, nb, W, n, next * TR, &tbar[(it + 1) & 1]);
-    if (!__syncthreads_and(tile_wait(&tbar[it & 1], (it >> 1) & 1, status))) {
+    if (!tile_wait_cta(&tbar[it & 1], (it >> 1) & 1, status)) {
       aborted = true;
       it_abort = it;
       left_after = next < ntiles;
@@ -745,7 +796,7 @@ __device__ __forceinline__ void k_tfinalize_dev(const int cta, const int ncta, i
   for (int it = 0; tile < ntiles; ++it, tile += ncta) {
     const int next = tile + ncta;
     if (next < ntiles) tile_load<T, TR>(stages + ((it + 1) & 1) * sstride, Q, bstride, nb, W, n, next * TR, &tbar[(it + 1) & 1]);
-    if (!__syncthreads_and(tile_wait(&tbar[it & 1], (it >> 1) & 1, status))) {
+    if (!tile_wait_cta(&tbar[it & 1], (it >> 1) & 1, status)) {
       aborted = true;
       it_abort = it;
       left_after = next < ntiles;
@@ -825,7 +876,7 @@ __device__ __forceinline__ void k_trestart_dev(const int cta, const int ncta, in
   for (int it = 0; tile < ntiles; ++it, tile += ncta) {
     const int next = tile + ncta;
     if (next < ntiles) tile_load<T, TR>(stages + ((it + 1) & 1) * sstride, Q, bstride, nbk, nullptr, n, next * TR, &tbar[(it + 1) & 1]);
-    if (!__syncthreads_and(tile_wait(&tbar[it & 1], (it >> 1) & 1, status))) {
+    if (!tile_wait_cta(&tbar[it & 1], (it >> 1) & 1, status)) {
       aborted = true;
       it_abort = it;
       left_after = next < ntiles;

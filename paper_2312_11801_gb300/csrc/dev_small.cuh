@@ -914,9 +914,13 @@ __device__ __forceinline__ double aug_at(const double* aug, int r, int c) {
 }
 
 // One CTA of 256 threads (8 warps: the phases below hand rows and scalars to fixed warps).
+// b1 = 1 solves App. B.1 instead: the model value f^_t(y~) = <b, y~> + max over the model set
+// of <C - A*(y~), X>, a linear objective over the same set, i.e. this IPM with Q11 = q12 =
+// q22 = 0 and the linear data of y~ (G^T y~ and <A Xbar, y~> from k_xupdate's sums in
+// red + RED_VEC); its value goes to sc->f_hat_ipm and the subproblem's S and eta are kept.
 __device__ __forceinline__ void k_ipm_dev(DevScalars* sc, const double* USBS_RESTRICT red, int kc,
                                              double alpha, double rho, double mu_tol, int max_iter,
-                                             int first_pass) {
+                                             int first_pass, int b1 = 0) {
   __shared__ IpmShared sh;
   const int tid = threadIdx.x;
   const int K = kc * (kc + 1) / 2;
@@ -936,12 +940,12 @@ __device__ __forceinline__ void k_ipm_dev(DevScalars* sc, const double* USBS_RES
   const double a2r = alpha * alpha / rho;
   for (int t = tid; t < K * K; t += blockDim.x) {
     const int i = t / K, j = t % K;
-    sh.Q[t] = a2r * aug_at(aug, sh.map[i], sh.map[j]);
+    sh.Q[t] = b1 ? 0.0 : a2r * aug_at(aug, sh.map[i], sh.map[j]);
   }
   if (tid < K) {
     const int gi = sh.map[tid];
-    sh.q12[tid] = has_eta ? a2r / tr * aug_at(aug, gi, 36) : 0.0;
-    const double gtw = first_pass ? aug_at(aug, gi, 37) : vec[gi];
+    sh.q12[tid] = (has_eta && !b1) ? a2r / tr * aug_at(aug, gi, 36) : 0.0;
+    const double gtw = (first_pass && !b1) ? aug_at(aug, gi, 37) : vec[gi];
     // svec of V^T C V (k_c x k_c block)
     int p = 0, q = 0;
     {
@@ -957,8 +961,9 @@ __device__ __forceinline__ void k_ipm_dev(DevScalars* sc, const double* USBS_RES
     sh.v[tid] = (p == q) ? 1.0 : 0.0;
   }
   if (tid == 0) {
-    sh.q22 = has_eta ? a2r / (tr * tr) * aug_at(aug, 36, 36) : 0.0;
-    const double axw = first_pass ? aug_at(aug, 36, 37) : vec[36];
+    sh.q22 = (has_eta && !b1) ? a2r / (tr * tr) * aug_at(aug, 36, 36) : 0.0;
+    // w = y - (b - nu)/rho for the subproblem; y~ itself for App. B.1 (vec[37] = <A Xbar, y~>)
+    const double axw = b1 ? vec[37] : (first_pass ? aug_at(aug, 36, 37) : vec[36]);
     sh.h2 = has_eta ? alpha * (axw - cx) / tr : 0.0;
     // strictly feasible start (App. B.1 leaves it free)
     for (int u = 0; u < 64; ++u) { sh.S[u] = 0.0; sh.T[u] = 0.0; }
@@ -1250,6 +1255,19 @@ __device__ __forceinline__ void k_ipm_dev(DevScalars* sc, const double* USBS_RES
     __syncthreads();
     if (sh.done) break;
   }
+  if (b1) {
+    if (tid == 0) {
+      // f^ = <b, y~> - min (h1^T svec S + eta h2)
+      double v = has_eta ? sh.eta * sh.h2 : 0.0;
+      int u = 0;
+      for (int q = 0; q < kc; ++q)
+        for (int p = q; p < kc; ++p, ++u) v = fma(sh.h1[u], (p == q ? 1.0 : SQ2) * sh.S[p * 8 + q], v);
+      sc->f_hat_ipm = vec[36] - v;
+      sc->ipm_iters_b1 = sh.iters;
+      if (!isfinite(sc->f_hat_ipm)) sc->status = USBS_ENUMERIC;
+    }
+    return;
+  }
   if (tid == 0) {
     for (int u = 0; u < 64; ++u) {
       sc->S_hat[u] = sh.S[u];
@@ -1269,7 +1287,7 @@ __device__ __forceinline__ void k_ipm_dev(DevScalars* sc, const double* USBS_RES
 // red + RED_VEC holds the reduced candidate sums of k_xupdate:
 // [0,36) G^T y~, 36 <b, y~>, 37 <A Xbar, y~>, 38 sum d^2, 39 max |d|.
 __device__ __forceinline__ void k_finish_dev(DevScalars* sc, const DevLanczos* lz, const double* USBS_RESTRICT red, int kc,
-                         double alpha, double beta, double bnorm) {
+                         double alpha, double beta, double bnorm, int use_ipm = 0) {
   __shared__ double Zs[64];
   __shared__ float Af[64], Vf[64];
   const double* vec = red + RED_VEC;
@@ -1303,7 +1321,10 @@ __device__ __forceinline__ void k_finish_dev(DevScalars* sc, const DevLanczos* l
   const double bty = vec[36], axy = vec[37];
   double best = fmax(0.0, lamV);
   if (sc->has_eta) best = fmax(best, (sc->cx - axy) / sc->tr);
-  const double f_hat = bty + alpha * best;
+  const double f_hat_closed = bty + alpha * best;
+  // App. B.1 by the IPM (launched before this kernel) in place of the closed form
+  const double f_hat = use_ipm ? sc->f_hat_ipm : f_hat_closed;
+  sc->f_hat_closed = f_hat_closed;
   const double lam = lz->theta[0];
   const double f_cand = alpha * fmax(lam, 0.0) + bty;
   const double f_old = sc->f_y;

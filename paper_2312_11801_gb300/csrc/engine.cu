@@ -412,6 +412,7 @@ static void fill_defaults(usbs_params* p) {
   p->certify_restarts = 0;
   p->certify_tol = 0.0;   // 0 = by precision
   p->obj_gap_tol = 0.0;
+  p->model_value_ipm = 0;
 }
 
 static int init_ctx(Ctx* c, int64_t n, int64_t m, int64_t nnzA, const usbs_params* p,
@@ -670,6 +671,8 @@ static void fill_info(Ctx* c, const DevScalars& s, int matvecs, usbs_step_info* 
   info->relinf_max = s.relinf_max;
   info->objective = s.cx_it * c->c_scale * c->tau;
   info->dual_bound = s.f_y * c->c_scale * c->tau;
+  info->f_hat_closed = s.f_hat_closed;
+  info->ipm_iters_b1 = s.ipm_iters_b1;
 }
 
 template <typename T>
@@ -713,6 +716,7 @@ static int step_impl(Ctx* c, usbs_step_info* info) {
   // eigen solve at the candidate
   LanczosOut lo;
   USBS_TRY(lanczos<T>(c, c->ycand, c->V, c->Vnew, &lo));
+  if (c->prm.model_value_ipm) launch_ipm_b1(c);
   launch_finish(c);
   launch_commit(c);
   if (c->kp == 0) {

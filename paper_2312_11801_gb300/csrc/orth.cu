@@ -65,7 +65,7 @@ void set_attrs() {
     cudaFuncSetAttribute(k_tupdate<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_tfinalize<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_trestart<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(sizeof(T) * (2 * (size_t)8 * BlockStride<T>::value + JMAX * 32)));
+                         (int)(sizeof(T) * (2 * (size_t)8 * BlockStride<T>::value) + 8 * JMAX * 32));
   });
 }
 
@@ -179,7 +179,8 @@ void Orth<T>::restart(Ctx* c, const void* Qb, int J, int nout, const double* Y, 
   USBS_LAUNCH_B(c, USBS_KIND_RESTART, 8.0 * sizeof(T) * c->n * (J / 8 + nout + (resid ? 2 : 0)));
   if (on_tc<T>(c) && tc_restart(c, Qb, J, nout, Y, out, resid, resid_slot)) return;
   set_attrs<T>();
-  const size_t sm = sizeof(T) * (2 * (size_t)(J / 8) * BlockStride<T>::value + (size_t)J * nout * 8);
+  // stages, then Y: J x 8 nout values (FP64), or (hi, lo) TF32 pairs (FP32), 8 bytes each
+  const size_t sm = sizeof(T) * (2 * (size_t)(J / 8) * BlockStride<T>::value) + 8 * (size_t)J * nout * 8;
   k_trestart<T><<<orth_grid(c, c->n, (const void*)k_trestart<T>, sm), 256, sm, c->stream>>>(
       (int)c->n, (const T*)Qb, (size_t)c->n * 8, J / 8, nout, Y, (T*)out, (size_t)c->n * 8,
       (const T*)resid, resid_slot, DEV_FIELD(c->lz, DevLanczos, status, int));
@@ -188,4 +189,51 @@ void Orth<T>::restart(Ctx* c, const void* Qb, int J, int nout, const double* Y, 
 template struct Orth<float>;
 template struct Orth<double>;
 
+namespace {
+// The bounded wait of the staged tiles, run alone: one CTA arms a stage barrier for a 1 KB
+// bulk copy and waits for it as every tile kernel does.  deliver = 0 issues no copy, so the
+// wait runs out, USBS_ETIMEOUT is written to *status and the abort path (a second bounded
+// wait, then the barriers released) runs; deliver = 1 issues the copy and the kernel ends
+// with *status untouched.
+__global__ void k_selftest_tile_wait(const float* __restrict__ src, int deliver, int* status) {
+  __shared__ __align__(128) float buf[256];
+  __shared__ uint64_t tbar[2];
+  tiles_begin(tbar);
+  if (threadIdx.x == 0) {
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    mbar_expect_tx(&tbar[0], 1024u);
+    if (deliver) bulk_g2s(buf, src, 1024u, &tbar[0]);
+  }
+  const bool ok = tile_wait_cta(&tbar[0], 0, status);
+  tiles_end(tbar, !ok, 0, 0, status);
+}
+}  // namespace
+
 }  // namespace usbs
+
+extern "C" int usbs_selftest_tile_wait(int deliver) {
+  using namespace usbs;
+  float* src = nullptr;
+  int* st = nullptr;
+  if (cudaMalloc(&src, 1024) != cudaSuccess || cudaMalloc(&st, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    if (src) cudaFree(src);
+    return USBS_ENOMEM;
+  }
+  int status = 0;
+  cudaError_t e = cudaMemset(src, 0, 1024);
+  if (e == cudaSuccess) e = cudaMemset(st, 0, sizeof(int));
+  if (e == cudaSuccess) {
+    k_selftest_tile_wait<<<1, 128>>>(src, deliver ? 1 : 0, st);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&status, st, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(src);
+  cudaFree(st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return USBS_ECUDA;
+  }
+  return status == USBS_ETIMEOUT ? USBS_ETIMEOUT : USBS_OK;
+}

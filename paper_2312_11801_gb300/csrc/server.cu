@@ -374,8 +374,8 @@ int usbs_batch_solve(usbs_ctx** ctxs, int count, double tol, int max_concurrency
   if (count == 0) return USBS_OK;
   for (int i = 0; i < count; ++i)
     if (!ctxs[i]) return USBS_EINVAL;
-  // contexts the persistent kernel can take, grouped by (precision, basis); one launch
-  // per group solves all of its instances
+  // contexts the persistent kernel can take, grouped by (precision, basis, size bucket);
+  // one launch (a replayed CUDA graph) per group solves all of its instances
   std::vector<std::vector<usbs::Ctx*>> groups;
   std::vector<std::vector<int>> group_idx;
   std::vector<int> rest;
@@ -384,7 +384,9 @@ int usbs_batch_solve(usbs_ctx** ctxs, int count, double tol, int max_concurrency
     if (!usbs::batch_eligible(c)) { rest.push_back(i); continue; }
     size_t g = 0;
     for (; g < groups.size(); ++g)
-      if (groups[g][0]->fp64 == c->fp64 && groups[g][0]->J == c->J) break;
+      if (groups[g][0]->fp64 == c->fp64 && groups[g][0]->J == c->J &&
+          usbs::batch_bucket(groups[g][0]->n) == usbs::batch_bucket(c->n))
+        break;
     if (g == groups.size()) { groups.emplace_back(); group_idx.emplace_back(); }
     groups[g].push_back(c);
     group_idx[g].push_back(i);

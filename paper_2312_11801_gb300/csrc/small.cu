@@ -37,13 +37,13 @@ __global__ void __launch_bounds__(J >= 64 ? 512 : 256, 1) k_ritz(DevLanczos* lz,
 
 __global__ void __launch_bounds__(256, 1) k_ipm(DevScalars* sc, const double* __restrict__ red, int kc,
                                              double alpha, double rho, double mu_tol, int max_iter,
-                                             int first_pass) {
-  k_ipm_dev(sc, red, kc, alpha, rho, mu_tol, max_iter, first_pass);
+                                             int first_pass, int b1) {
+  k_ipm_dev(sc, red, kc, alpha, rho, mu_tol, max_iter, first_pass, b1);
 }
 
 __global__ void k_finish(DevScalars* sc, const DevLanczos* lz, const double* __restrict__ red, int kc,
-                         double alpha, double beta, double bnorm) {
-  k_finish_dev(sc, lz, red, kc, alpha, beta, bnorm);
+                         double alpha, double beta, double bnorm, int use_ipm) {
+  k_finish_dev(sc, lz, red, kc, alpha, beta, bnorm, use_ipm);
 }
 
 __global__ void k_certify(DevScalars* sc, const DevLanczos* lz, const double* __restrict__ red,
@@ -128,12 +128,19 @@ void launch_ritz(Ctx* c, int J, int keep, int spec) {
 void launch_ipm(Ctx* c, int first_pass) {
   USBS_LAUNCH(c, USBS_KIND_SMALL);
   k_ipm<<<1, 256, 0, c->stream>>>(c->sc, c->red, c->kdim, c->alpha, c->prm.rho, c->prm.ipm_mu_tol,
-                                  c->prm.ipm_max_iter, first_pass);
+                                  c->prm.ipm_max_iter, first_pass, 0);
+}
+
+void launch_ipm_b1(Ctx* c) {
+  USBS_LAUNCH(c, USBS_KIND_SMALL);
+  k_ipm<<<1, 256, 0, c->stream>>>(c->sc, c->red, c->kdim, c->alpha, c->prm.rho, c->prm.ipm_mu_tol,
+                                  c->prm.ipm_max_iter, 0, 1);
 }
 
 void launch_finish(Ctx* c) {
   USBS_LAUNCH(c, USBS_KIND_SMALL);
-  k_finish<<<1, 32, 0, c->stream>>>(c->sc, c->lz, c->red, c->kdim, c->alpha, c->prm.beta, c->bnorm);
+  k_finish<<<1, 32, 0, c->stream>>>(c->sc, c->lz, c->red, c->kdim, c->alpha, c->prm.beta, c->bnorm,
+                                    c->prm.model_value_ipm);
 }
 
 void launch_certify(Ctx* c) {

@@ -31,7 +31,7 @@ class usbs_params(ctypes.Structure):
                 ("trace_hint", ctypes.c_double), ("max_iters", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p), ("device", ctypes.c_int),
                 ("certify_restarts", ctypes.c_int), ("certify_tol", ctypes.c_double),
-                ("obj_gap_tol", ctypes.c_double)]
+                ("obj_gap_tol", ctypes.c_double), ("model_value_ipm", ctypes.c_int)]
 
 
 class usbs_eig_info(ctypes.Structure):
@@ -47,7 +47,8 @@ class usbs_step_info(ctypes.Structure):
                 ("lambda_max", ctypes.c_double), ("cx", ctypes.c_double), ("trx", ctypes.c_double),
                 ("eta", ctypes.c_double), ("relgap", ctypes.c_double), ("relinf", ctypes.c_double),
                 ("relinf_max", ctypes.c_double), ("objective", ctypes.c_double),
-                ("dual_bound", ctypes.c_double)]
+                ("dual_bound", ctypes.c_double), ("f_hat_closed", ctypes.c_double),
+                ("ipm_iters_b1", ctypes.c_int)]
 
 
 class usbs_result(ctypes.Structure):
@@ -111,6 +112,7 @@ SIGNATURES = [
     ("usbs_get_sketch", ctypes.c_int, [_P, _F, _F, _D]),
     ("usbs_nystrom_round", ctypes.c_int, [_P, _D, _D, _D, ctypes.POINTER(ctypes.c_int),
                                           ctypes.POINTER(ctypes.c_int8)]),
+    ("usbs_qap_round", ctypes.c_int, [_P, ctypes.c_int, _D, _D, _D, _D, _I32, ctypes.POINTER(ctypes.c_int)]),
     ("usbs_get_dual", ctypes.c_int, [_P, _D]),
     ("usbs_get_primal_constraints", ctypes.c_int, [_P, _D]),
     ("usbs_state_size", ctypes.c_int64, [_P]),
@@ -126,6 +128,7 @@ SIGNATURES = [
     ("usbs_profile", ctypes.c_int, [_P, ctypes.c_int]),
     ("usbs_kernel_stats", ctypes.c_int, [_P, ctypes.c_int, _D, ctypes.POINTER(ctypes.c_longlong), _D]),
     ("usbs_launch_count", ctypes.c_longlong, [_P]),
+    ("usbs_selftest_tile_wait", ctypes.c_int, [ctypes.c_int]),
     ("usbs_instance_bytes", ctypes.c_uint64, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                               ctypes.c_int64, ctypes.c_int, ctypes.c_int]),
     ("usbs_server_params_default", None, [ctypes.POINTER(usbs_server_params)]),
@@ -314,6 +317,21 @@ def usbs_nystrom_round(ctx, want_u=True, want_signs=True):
     return lam, U, vals, best.value, z
 
 
+def usbs_qap_round(ctx, W, D):
+    """QAP rounding of the sketch: (costs, scores, perms (r x nq), best column)."""
+    W = np.ascontiguousarray(W, np.float64)
+    D = np.ascontiguousarray(D, np.float64)
+    nq = W.shape[0]
+    costs = np.zeros(ctx.r)
+    scores = np.zeros(ctx.r)
+    perms = np.zeros((ctx.r, nq), np.int32)
+    best = ctypes.c_int()
+    _check(load().usbs_qap_round(ctx.ptr, nq, _ptr(W, ctypes.c_double), _ptr(D, ctypes.c_double),
+                                 _ptr(costs, ctypes.c_double), _ptr(scores, ctypes.c_double),
+                                 _ptr(perms, ctypes.c_int32), ctypes.byref(best)), ctx.ptr)
+    return costs, scores, perms, best.value
+
+
 def usbs_get_dual(ctx):
     y = np.zeros(ctx.m)
     _check(load().usbs_get_dual(ctx.ptr, _ptr(y, ctypes.c_double)), ctx.ptr)
@@ -398,6 +416,11 @@ def usbs_kernel_stats(ctx):
 
 def usbs_launch_count(ctx):
     return int(load().usbs_launch_count(ctx.ptr))
+
+
+def usbs_selftest_tile_wait(deliver):
+    """The staged tiles' bounded wait run alone; returns the status code (no exception)."""
+    return load().usbs_selftest_tile_wait(int(bool(deliver)))
 
 
 def usbs_sketch_update_static(n, r, V_dev, S_dev, Psi_dev, P_dev, eta, stream=None):

@@ -9,7 +9,7 @@ Calls only oracle/ and the input generators (paper_2312_11801_gb300.instances). 
                  (k = 8, rho = 0.01, no sketch): per-step f(y), <C,X>, tr X, lambda_max,
                  relative infeasibility, model value and descent flag;
   er6000_solve   a solve of MaxCut on an Erdos-Renyi graph, n = 6000, average degree 6,
-                 to both gates <= 3e-4 (rho = 0.1).
+                 to both gates <= 1e-3 (rho = 0.1, at most 800 iterations).
 Usage: python tests/golden/make_large_golden.py [case ...]
 """
 import json
@@ -65,7 +65,7 @@ def traj_case(pname, steps=6):
             "seconds": time.time() - t0}
 
 
-def solve_case(pname, tol=3e-4, max_iters=3000):
+def solve_case(pname, tol=1e-3, max_iters=800):
     prob = PROBLEMS[pname]()
     o = OU.USBSOracle(prob, k=8, rho=0.1)
     t0 = time.time()

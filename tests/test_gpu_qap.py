@@ -1,0 +1,120 @@
+"""The synthetic QAP relaxation (App. E, eq. qap_sdp) on the GPU: constraints with many
+entries each (partial traces, row and column sums, gangster and sign rows), the iteration
+against the oracle, weak duality against the brute-force optimum, and the QAP rounding of
+the sketch (Nystrom reconstruction, then the Hungarian projection of every column) on the
+device against the same rounding computed on the host from the same factor U."""
+import itertools
+
+import numpy as np
+import pytest
+import scipy.optimize as so
+
+from oracle import usbs as OU
+from oracle.nystrom import qap_cost
+from oracle.usbs import USBSOracle
+from paper_2312_11801_gb300 import instances as I
+from tests.gpu_util import bulk_dtype, gpu_modules, rel_err
+
+pytestmark = pytest.mark.gpu
+NQ = 6
+
+
+@pytest.fixture(scope="module")
+def mods():
+    return gpu_modules()
+
+
+def _opt_cost(W, D):
+    nq = W.shape[0]
+    return min(np.trace(W @ np.eye(nq)[list(p)] @ D @ np.eye(nq)[list(p)].T)
+               for p in itertools.permutations(range(nq)))
+
+
+def test_qap_step_trajectory_fp64(mods):
+    """Eight iterations (with the alternation over the inequality rows) equal the oracle's."""
+    torch, U = mods
+    prob = I.qap_sdp(NQ, 0)
+    ora = USBSOracle(prob, k=8, rho=0.1)
+    ora.cold_start()
+    with U.usbs_create(prob, precision=0, rho=0.1, lanczos_restarts=300, lanczos_tol=1e-12,
+                       trace_hint=prob.trace) as ctx:
+        for t in range(8):
+            g = U.usbs_step(ctx)
+            o = ora.step()
+            assert g["n_alt"] == o["n_alt"] and g["descent"] == int(o["descent"]), t
+            for kg, ko in [("f_y", "f_y"), ("cx", "cx"), ("trx", "trX"), ("relinf", "relinf")]:
+                assert abs(g[kg] - o[ko]) <= 1e-6 * (1 + abs(o[ko])), (t, kg, g[kg], o[ko])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_qap_constraint_eval(mods, precision):
+    """a9 on constraints of many entries: z = A(V S V^T) against the oracle's."""
+    torch, U = mods
+    prob = I.qap_sdp(NQ, 1)
+    sp_ = OU.scale_problem(prob)
+    rng = np.random.default_rng(4)
+    V, _ = np.linalg.qr(rng.standard_normal((prob.n, 8)))
+    S = rng.standard_normal((8, 8)); S = S + S.T
+    dt = bulk_dtype(torch, precision)
+    Vr = torch.tensor(V, dtype=dt).double().numpy()
+    ref = OU.A_lowrank(sp_, Vr, S)
+    with U.usbs_create(prob, precision=precision, trace_hint=prob.trace) as ctx:
+        z = torch.zeros(prob.m, dtype=torch.float64, device="cuda")
+        U.usbs_op_constraint_eval(ctx, torch.tensor(V, dtype=dt, device="cuda"),
+                                  torch.tensor(S, dtype=torch.float64, device="cuda"), z)
+        torch.cuda.synchronize()
+        got = z.cpu().numpy()
+    assert rel_err(got, ref) <= (1e-11 if precision == 0 else 2e-4)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_qap_solve_bound_and_rounding(mods, precision):
+    """A capped solve: its dual bound stays above minus the optimal cost (weak duality,
+    checked at every iteration), and the device rounding of its sketch gives, column by
+    column, an assignment of maximal <M_k, Pi> (the same value as the host's Hungarian
+    method on the same U) priced at tr(W Pi D Pi^T), never below the optimum."""
+    torch, U = mods
+    prob = I.qap_sdp(NQ, 0)
+    W, D = prob.meta["W"], prob.meta["D"]
+    opt = _opt_cost(W, D)
+    r = 6
+    psi = I.gaussian_psi(prob.n, r, seed=3)
+    with U.usbs_create(prob, psi=psi, r=r, precision=precision, rho=0.1, trace_hint=prob.trace) as ctx:
+        for _ in range(150):
+            s = U.usbs_step(ctx)
+            # f(y) from a converged eigen solve: FP64 exact to rounding, mixed to the FP32
+            # residual of its Ritz value (1e-4 of the cost scale)
+            assert s["dual_bound"] >= -opt - (1e-9 if precision == 0 else 1e-4) * opt, s
+        costs, scores, perms, best = U.usbs_qap_round(ctx, W, D)
+        lam, Uf, _, _, _ = U.usbs_nystrom_round(ctx, want_u=True, want_signs=False)
+    for k in range(r):
+        sgn = 1.0 if Uf[0, k] >= 0 else -1.0
+        M = (sgn * Uf[1:, k]).reshape((NQ, NQ), order="F")
+        rows, cols = so.linear_sum_assignment(-M)
+        assert abs(scores[k] - M[rows, cols].sum()) <= 1e-9 * (1 + abs(scores[k])), k
+        Pi = np.zeros((NQ, NQ))
+        Pi[np.arange(NQ), perms[k]] = 1.0
+        assert np.allclose(Pi.sum(0), 1) and np.allclose(Pi.sum(1), 1)
+        assert abs(np.sum(M * Pi) - scores[k]) <= 1e-9 * (1 + abs(scores[k]))
+        assert costs[k] == qap_cost(W, D, Pi)
+        assert costs[k] >= opt - 1e-9
+    assert costs[best] == costs.min()
+
+
+def test_qap_rounding_recovers_a_permutation_point(mods):
+    """With the sketch of X_Pi itself (rank one) the device rounding returns Pi at its cost."""
+    torch, U = mods
+    prob = I.qap_sdp(NQ, 2)
+    W, D = prob.meta["W"], prob.meta["D"]
+    perm = (3, 0, 5, 1, 2, 4)
+    Pi = np.eye(NQ)[list(perm)]
+    v = np.concatenate([[1.0], Pi.flatten(order="F")])
+    r = 4
+    psi = I.gaussian_psi(prob.n, r, seed=5)
+    with U.usbs_create(prob, psi=psi, r=r, precision=1, trace_hint=prob.trace) as ctx:
+        st = U.usbs_get_state(ctx)
+        st[-prob.n * r:] = (np.outer(v, v) @ psi.astype(np.float64)).ravel()
+        U.usbs_set_state(ctx, st)
+        costs, scores, perms, best = U.usbs_qap_round(ctx, W, D)
+    assert list(perms[best]) == list(perm)
+    assert costs[best] == qap_cost(W, D, Pi)
