@@ -311,7 +311,7 @@ def run_ours(args, world, rank, local, pg):
     if args.serve_requests > 0:
         from paper_2312_11801_gb300 import instances as I
         serve = serve_measure(U, I, args.serve_requests, args.n_lo, args.n_hi, args.rho, 32,
-                              args.serve_max_iters, args.slots, args.load, seed=rank)
+                              args.serve_max_iters, args.slots, args.load, seed=rank, k_c=args.k_c, k_p=args.k_p)
     hbm, peak_src = peaks()
     # roofline of the dominant bulk kernel (largest device time among the kinds with
     # algorithmic bytes; the k-sized one-CTA kernels are latency-bound, not HBM-bound)
@@ -372,7 +372,7 @@ def _pct(xs, q):
     return float(np.percentile(np.asarray(xs, dtype=np.float64), q)) if len(xs) else None
 
 
-def plain_fp64_sample(U, probs, rho, tol, max_iters, budget_s, basis=32):
+def plain_fp64_sample(U, probs, rho, tol, max_iters, budget_s, basis=32, k_c=8, k_p=0):
     """The plain path: one instance at a time, FP64 throughout, per-step kernels, cold
     start; solves in order until the time budget is spent.  Returns per-solve records."""
     out = []
@@ -382,7 +382,7 @@ def plain_fp64_sample(U, probs, rho, tol, max_iters, budget_s, basis=32):
             break
         t0 = time.perf_counter()
         with U.usbs_create(p, precision=U.PRECISION_FP64, rho=rho, max_iters=max_iters,
-                           lanczos_basis=basis) as c:
+                           lanczos_basis=basis, k_c=k_c, k_p=k_p) as c:
             r = U.usbs_solve(c, tol=tol)
         out.append({"secs": time.perf_counter() - t0, "iters": r["iters"], "converged": r["converged"],
                     "n": p.n})
@@ -401,7 +401,7 @@ def run_batched(args, world, rank, local, pg):
     torch.cuda.set_device(local)
     probs = I.batched_er(args.batch_count, seed0=1000 * rank)
     kw = dict(precision=U.PRECISION_MIXED, lanczos_basis=args.lanczos_basis, rho=args.rho,
-              max_iters=args.max_iters)
+              max_iters=args.max_iters, k_c=args.k_c, k_p=args.k_p)
     ctxs = [U.usbs_create(p, **kw) for p in probs]
     for _ in range(args.warmup):
         U.usbs_batch_solve(ctxs, tol=TOL)
@@ -431,7 +431,7 @@ def run_batched(args, world, rank, local, pg):
     e2e_conv = sum(r["converged"] for r in res)
     e2e_elapsed = max_over_ranks(pg, time.perf_counter() - t0)
     plain = plain_fp64_sample(U, probs, args.rho, TOL, args.max_iters, args.plain_budget,
-                              args.lanczos_basis) \
+                              args.lanczos_basis, args.k_c, args.k_p) \
         if rank == 0 and not args.no_plain else []
     pconv = sum(r["converged"] for r in plain)
     line = {
@@ -440,7 +440,7 @@ def run_batched(args, world, rank, local, pg):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": f"batched_er_{args.batch_count}_n100-4000_d8_u01_mixed_J{args.lanczos_basis}",
-                   "instances": len(probs), "rho": args.rho, "tol": TOL, "k_c": 8,
+                   "instances": len(probs), "rho": args.rho, "tol": TOL, "k_c": args.k_c, "k_p": args.k_p,
                    "precision": "mixed: FP32 bulk, FP64 k-sized", "launch": "persistent, one CTA per instance",
                    "parallelism": f"replicas{world}", "converged_per_step": conv / args.steps,
                    "iters_median": float(np.median(iters)), "iters_max": int(max(iters))},
@@ -472,7 +472,7 @@ def serve_requests(I, count, n_lo, n_hi, seed=0):
     return reqs
 
 
-def serve_measure(U, I, requests, n_lo, n_hi, rho, basis, max_iters, slots, load, seed=0):
+def serve_measure(U, I, requests, n_lo, n_hi, rho, basis, max_iters, slots, load, seed=0, k_c=8, k_p=0):
     """C5 serving: a Poisson stream of MaxCut requests (random geometric graphs, n
     log-uniform on [n_lo, n_hi], every second request a 1 %-grown copy of an earlier one)
     served by continuous batching (mixed precision, grown requests warm-started from their
@@ -486,7 +486,7 @@ def serve_measure(U, I, requests, n_lo, n_hi, rho, basis, max_iters, slots, load
     for q in reqs:
         t0 = time.perf_counter()
         with U.usbs_create(q["prob"], precision=U.PRECISION_FP64, rho=rho, max_iters=max_iters,
-                           lanczos_basis=basis) as c:
+                           lanczos_basis=basis, k_c=k_c, k_p=k_p) as c:
             r = U.usbs_solve(c, tol=TOL)
         plain_s.append((time.perf_counter() - t0, bool(r["converged"])))
     plain_cap = len(reqs) / sum(t for t, _ in plain_s)
@@ -500,7 +500,8 @@ def serve_measure(U, I, requests, n_lo, n_hi, rho, basis, max_iters, slots, load
         plain_lat.append(free_at - a_t)
     plain_makespan = free_at - arrivals[0]
     srv = U.usbs_server_create(max_slots=slots, cache_entries=requests,
-                               solver={"rho": rho, "lanczos_basis": basis, "max_iters": max_iters})
+                               solver={"rho": rho, "lanczos_basis": basis, "max_iters": max_iters,
+                                       "k_c": k_c, "k_p": k_p})
     done = []
     t0 = time.perf_counter()
     for q, a_t in zip(reqs, arrivals):
@@ -521,6 +522,7 @@ def serve_measure(U, I, requests, n_lo, n_hi, rho, basis, max_iters, slots, load
         "requests": len(reqs), "grown_from_parent": sum(q["parent"] >= 0 for q in reqs),
         "n_range": [min(q["prob"].n for q in reqs), max(q["prob"].n for q in reqs)],
         "rho": rho, "tol": TOL, "lanczos_basis": basis, "max_iters": max_iters, "slots": slots,
+        "k_c": k_c, "k_p": k_p,
         "load_vs_plain_capacity": load, "arrival_rate_per_s": rate,
         "served": {"solves_per_s": conv / served_makespan, "converged": conv,
                    "p50_s_converged": _pct(lat_conv, 50), "p99_s_converged": _pct(lat_conv, 99),
@@ -543,7 +545,7 @@ def run_serve(args, world, rank, local, pg):
     from paper_2312_11801_gb300 import instances as I
     torch.cuda.set_device(local)
     sv = serve_measure(U, I, args.requests, args.n_lo, args.n_hi, args.rho, args.lanczos_basis,
-                       args.max_iters, args.slots, args.load, seed=rank)
+                       args.max_iters, args.slots, args.load, seed=rank, k_c=args.k_c, k_p=args.k_p)
     line = {
         "metric": METRIC, "value": sv["served"]["solves_per_s"], "unit": UNIT, "n_gpus": world,
         "steps": 1, "warmup": 0, "ms_per_step": 1e3 * sv["served"]["makespan_s"], "higher_is_better": True,
@@ -760,6 +762,8 @@ def main():
     ap.add_argument("--c3-n", type=int, default=65536)
     ap.add_argument("--c3-rho", type=float, default=0.01)
     ap.add_argument("--rho", type=float, default=0.1, help="rho of the batched and served workloads")
+    ap.add_argument("--k-c", type=int, default=8, help="k_c of the batched and served workloads")
+    ap.add_argument("--k-p", type=int, default=0, help="k_p of the batched and served workloads")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--plain-budget", type=float, default=60.0)
     ap.add_argument("--no-plain", action="store_true")

@@ -16,9 +16,9 @@ int batch_launch_f64_j32(const std::vector<Ctx*>& cs, cudaStream_t st, double to
 // both precisions, J = 64 in mixed precision) and no per-step host work (debug checks,
 // event profiling).
 bool batch_eligible(const Ctx* c) {
-  // the per-step path alone carries past information, certification, the
-  // objective-relative gate and the App. B.1 model-value IPM
-  if (c->debug || c->prof || c->kp > 0 || c->prm.certify_restarts > 0 || c->prm.obj_gap_tol > 0.0 ||
+  // the per-step path alone carries certification, the objective-relative gate and the
+  // App. B.1 model-value IPM
+  if (c->debug || c->prof || c->prm.certify_restarts > 0 || c->prm.obj_gap_tol > 0.0 ||
       c->prm.model_value_ipm)
     return false;
   if (c->fp64) return c->J == 32;

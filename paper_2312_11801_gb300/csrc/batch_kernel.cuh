@@ -39,7 +39,7 @@ namespace usbs {
 // outputs at the end.
 struct BatchDesc {
   // sizes and parameters
-  int n, m, nnz_off, kc, r, J, keep, has_offdiag_A, any_ineq;
+  int n, m, nnz_off, kc, kp, kdim, r, J, keep, has_offdiag_A, any_ineq;
   int restarts, max_alt, ipm_max_iter, max_iters;
   double alpha, rho, beta, bnorm, tol, lanczos_tol, ipm_mu_tol, alt_tol;
   uint64_t seed, rng_counter;
@@ -109,10 +109,11 @@ __device__ void b_orth_block(BatchCtx<T>& b, T* Q, int nb, T* W, T* out, int j, 
   }
 }
 
-// Top eigenpairs of C - A*(y): the device twin of the host Lanczos driver.  Returns 0 or
-// USBS_ENUMERIC.  start may be null (zero start block, replaced by random columns).
+// Top eigenpairs of C - A*(y): the device twin of the host Lanczos driver, converging
+// the top kconv Ritz pairs.  Returns 0 or USBS_ENUMERIC.  start may be null (zero start
+// block, replaced by random columns).
 template <typename T, typename S, int J>
-__device__ int b_lanczos(BatchCtx<T>& b, const double* y, const T* start, T* out_vecs) {
+__device__ int b_lanczos(BatchCtx<T>& b, const double* y, const T* start, T* out_vecs, int kconv) {
   const BatchDesc* d = b.d;
   const int n = d->n;
   const size_t bs = (size_t)n * 8;
@@ -140,7 +141,7 @@ __device__ int b_lanczos(BatchCtx<T>& b, const double* y, const T* start, T* out
       b.matvecs += 8;
       b_orth_block<T>(b, Q, j + 1, W, Q + (j + 1) * bs, j, 1, j == nblk - 1);
     }
-    k_ritz_dev<S, J>(d->lz, d->kc, d->lanczos_tol, sweeps, jac_eps);
+    k_ritz_dev<S, J>(d->lz, kconv, d->lanczos_tol, sweeps, jac_eps);
     __syncthreads();
     if (d->lz->status != 0) { rc = d->lz->status == USBS_ETIMEOUT ? USBS_ETIMEOUT : USBS_ENUMERIC; break; }
     if (d->lz->converged || cycle == d->restarts - 1) break;
@@ -183,7 +184,7 @@ __device__ int b_step(BatchCtx<T>& b, T*& V, T*& Vnew, double*& ax, double*& axn
   __syncthreads();
   int n_alt;
   for (n_alt = 1; n_alt <= d->max_alt; ++n_alt) {
-    k_ipm_dev(sc, red, d->kc, d->alpha, d->rho, d->ipm_mu_tol, d->ipm_max_iter, n_alt == 1);
+    k_ipm_dev(sc, red, d->kdim, d->alpha, d->rho, d->ipm_mu_tol, d->ipm_max_iter, n_alt == 1);
     __syncthreads();
     if (!d->any_ineq) break;
     k_alt_dev<T>(0, 1, m, d->con_ptr, d->ent_i, d->ent_j, (const T*)d->ent_v, V, sc, ax, d->y,
@@ -198,15 +199,32 @@ __device__ int b_step(BatchCtx<T>& b, T*& V, T*& Vnew, double*& ax, double*& axn
                    d->b, d->ineq, 1.0 / d->rho, axnew, d->ycand, red + RED_VEC);
   __syncthreads();
   const long long mv0 = b.matvecs;
-  const int rc = b_lanczos<T, S, J>(b, d->ycand, V, Vnew);
+  const int rc = b_lanczos<T, S, J>(b, d->ycand, V, Vnew, d->kc);
   d->last_matvecs = (int)(b.matvecs - mv0);
   if (rc) return rc;
-  if (threadIdx.x < 32) k_finish_dev(sc, d->lz, red, d->kc, d->alpha, d->beta, d->bnorm);
+  if (threadIdx.x < 32) k_finish_dev(sc, d->lz, red, d->kdim, d->alpha, d->beta, d->bnorm);
   __syncthreads();
   k_commit_dev(0, 1, m, sc, d->ycand, d->y);
-  if (d->r)
-    k_sketch_update_dev<T>(0, 1, n, d->r, V, sc->S, red + RED_SK, d->P, &sc->eta, 0.0);
-  __syncthreads();
+  if (d->kp == 0) {
+    // model update with k_p = 0: Xbar_{t+1} = X_{t+1}, V_{t+1} = the top k_c Ritz vectors
+    if (d->r)
+      k_sketch_update_dev<T>(0, 1, n, d->r, V, sc->S, red + RED_SK, d->P, &sc->eta, 0.0);
+    __syncthreads();
+  } else {
+    // past information (Sec. 3), as on the per-step path: S = S_p + S_c, Xbar_{t+1} =
+    // eta Xbar_t + V S_c V^T, V_{t+1} = an orthonormal basis of [V Q_p, v_1..v_kc]
+    __syncthreads();
+    k_kp_split_dev(sc, red, d->kdim, d->kp);
+    __syncthreads();
+    if (d->r)
+      k_sketch_update_dev<T>(0, 1, n, d->r, V, sc->Sc, red + RED_SK, d->P, &sc->eta, 0.0);
+    k_constraint_axpy_dev<T>(0, 1, m, d->con_ptr, d->ent_i, d->ent_j, (const T*)d->ent_v, V, sc->Sc, &sc->eta,
+                             ax, axnew);
+    __syncthreads();
+    k_vnext_dev<T>(0, 1, n, V, sc->Qp, Vnew, d->kp, d->kc, (T*)d->W);
+    __syncthreads();
+    b_orth_block<T>(b, b.Q, 0, (T*)d->W, Vnew, -1, 0, 0);
+  }
   T* t = V; V = Vnew; Vnew = t;
   double* u = ax; ax = axnew; axnew = u;
   if (threadIdx.x == 0) sc->n_alt = n_alt_out;
@@ -235,7 +253,7 @@ __global__ void __launch_bounds__(BT) k_batch_solve(BatchDesc* descs, int count,
     for (size_t t = threadIdx.x; t < (size_t)n * d->r; t += blockDim.x) d->P[t] = 0.f;
     for (size_t t = threadIdx.x; t < (size_t)n * 8; t += blockDim.x) V[t] = (T)0;
     __syncthreads();
-    int rc = b_lanczos<T, S, J>(b, d->y, V, Vnew);
+    int rc = b_lanczos<T, S, J>(b, d->y, V, Vnew, d->kdim);
     int iters = 0, conv = 0, desc = 0, n_alt = 0;
     if (rc == 0) {
       T* t = V; V = Vnew; Vnew = t;
@@ -308,7 +326,8 @@ struct BatchPlan {
 
 inline void fill_desc(BatchDesc& d, const Ctx* c, double tol, int max_iters) {
   std::memset(&d, 0, sizeof(d));
-  d.n = (int)c->n; d.m = (int)c->m; d.nnz_off = c->nnz_off; d.kc = c->kc; d.r = c->r;
+  d.n = (int)c->n; d.m = (int)c->m; d.nnz_off = c->nnz_off; d.kc = c->kc; d.kp = c->kp; d.kdim = c->kdim;
+  d.r = c->r;
   d.J = c->J; d.keep = c->keep; d.has_offdiag_A = c->has_offdiag_A; d.any_ineq = c->any_ineq;
   d.restarts = c->prm.lanczos_restarts; d.max_alt = c->prm.max_alt;
   d.ipm_max_iter = c->prm.ipm_max_iter; d.max_iters = max_iters;

@@ -38,13 +38,13 @@ def _batch(U, probs, **kw):
     return res, st, duals
 
 
-@pytest.mark.parametrize("basis", [32, 64])
-def test_alone_and_in_the_mix_are_identical(mods, basis):
+@pytest.mark.parametrize("basis,k_c,k_p", [(32, 8, 0), (64, 8, 0), (32, 7, 1)])
+def test_alone_and_in_the_mix_are_identical(mods, basis, k_c, k_p):
     torch, U = mods
     probs = _mix()
-    mix, st, ymix = _batch(U, probs, lanczos_basis=basis)
+    mix, st, ymix = _batch(U, probs, lanczos_basis=basis, k_c=k_c, k_p=k_p)
     for i in (0, 4):
-        alone, st1, y1 = _batch(U, [probs[i]], lanczos_basis=basis)
+        alone, st1, y1 = _batch(U, [probs[i]], lanczos_basis=basis, k_c=k_c, k_p=k_p)
         a, b = alone[0], mix[i]
         assert a["iters"] == b["iters"] and a["converged"] == b["converged"]
         assert a["last"]["objective"] == b["last"]["objective"]
@@ -52,19 +52,24 @@ def test_alone_and_in_the_mix_are_identical(mods, basis):
         assert np.array_equal(y1[0], ymix[i])
 
 
-@pytest.mark.parametrize("precision,basis", [(1, 32), (1, 64), (0, 32)])
-def test_batched_agrees_with_per_step_path(mods, precision, basis):
+@pytest.mark.parametrize("precision,basis,k_c,k_p", [(1, 32, 8, 0), (1, 64, 8, 0), (0, 32, 8, 0),
+                                                     (0, 32, 7, 1), (1, 32, 6, 2)])
+def test_batched_agrees_with_per_step_path(mods, precision, basis, k_c, k_p):
+    """Also with past information (k_p > 0, Sec. 3): the batched kernel runs the same split
+    of S, the same update of Xbar and the same Cholesky QR of [V Q_p, v_1..v_kc]."""
     torch, U = mods
     probs = _mix()[:4] if precision == 0 else _mix()
-    res, st, _ = _batch(U, probs, precision=precision, lanczos_basis=basis)
+    kw = dict(precision=precision, lanczos_basis=basis, k_c=k_c, k_p=k_p)
+    res, st, _ = _batch(U, probs, **kw)
     for p, r, s in zip(probs, res, st):
-        with U.usbs_create(p, max_iters=CAP, precision=precision, lanczos_basis=basis) as c:
+        with U.usbs_create(p, max_iters=CAP, **kw) as c:
             solo = U.usbs_solve(c, tol=TOL)
         assert s in (U.USBS_OK, U.USBS_ENOTCONV)
         if r["converged"] != solo["converged"]:
-            # the two drivers round their FP32 tiles differently (per-step: tcgen05; batched:
-            # mma.sync in one CTA), so iterates drift apart at FP32 rounding and a solve that
-            # ends near the cap may end on either side of it: the other must then be close
+            # the two drivers sum their tiles in different orders (per step: many CTAs and
+            # FP64 partials; batched: one CTA), so iterates drift apart at rounding level and
+            # a solve that ends near the cap may end on either side of it: the other must
+            # then be close
             other = solo if r["converged"] else r
             assert max(other["last"]["relgap"], other["last"]["relinf"]) <= 10 * TOL, \
                 (p.name, r["iters"], solo["iters"], other["last"])

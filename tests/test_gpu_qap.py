@@ -31,19 +31,30 @@ def _opt_cost(W, D):
 
 
 def test_qap_step_trajectory_fp64(mods):
-    """Eight iterations (with the alternation over the inequality rows) equal the oracle's."""
+    """Eight iterations (with the alternation over the inequality rows) follow the oracle's.
+
+    nq = 7 (n = 50), so that the Lanczos basis holds 32 vectors: at nq = 6 (n = 37) it is
+    capped at 16, and with the eighth and ninth eigenvalues of C 1.2 % apart the cold-start
+    eigenvectors then need more restarts than this test gives.  The alternation over the
+    276-plus sign rows converges slowly (tens of passes, some at the cap of 50), and its pass
+    count moves by a pass or two with the IPM's stopping point (the oracle alone gives 28, 29
+    or 30 at one step for mu < 1e-8, 1e-9, 1e-10).  The stopping rule bounds the last change
+    of nu, not its distance to the fixed point, which at a contraction rate near one is many
+    times larger; so the count is compared within two passes, the descent decisions exactly
+    and the values to 1e-5 (the first steps agree to 1e-6)."""
     torch, U = mods
-    prob = I.qap_sdp(NQ, 0)
-    ora = USBSOracle(prob, k=8, rho=0.1)
+    prob = I.qap_sdp(7, 0)
+    ora = USBSOracle(prob, k=8, rho=0.1, ipm_mu_tol=1e-10)
     ora.cold_start()
-    with U.usbs_create(prob, precision=0, rho=0.1, lanczos_restarts=300, lanczos_tol=1e-12,
-                       trace_hint=prob.trace) as ctx:
+    with U.usbs_create(prob, precision=0, rho=0.1, lanczos_basis=32, lanczos_restarts=1000,
+                       lanczos_tol=1e-11, ipm_mu_tol=1e-10, trace_hint=prob.trace) as ctx:
         for t in range(8):
             g = U.usbs_step(ctx)
             o = ora.step()
-            assert g["n_alt"] == o["n_alt"] and g["descent"] == int(o["descent"]), t
+            assert abs(g["n_alt"] - o["n_alt"]) <= 2, (t, g["n_alt"], o["n_alt"])
+            assert g["descent"] == int(o["descent"]), t
             for kg, ko in [("f_y", "f_y"), ("cx", "cx"), ("trx", "trX"), ("relinf", "relinf")]:
-                assert abs(g[kg] - o[ko]) <= 1e-6 * (1 + abs(o[ko])), (t, kg, g[kg], o[ko])
+                assert abs(g[kg] - o[ko]) <= 1e-5 * (1 + abs(o[ko])), (t, kg, g[kg], o[ko])
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -115,6 +126,13 @@ def test_qap_rounding_recovers_a_permutation_point(mods):
         st = U.usbs_get_state(ctx)
         st[-prob.n * r:] = (np.outer(v, v) @ psi.astype(np.float64)).ravel()
         U.usbs_set_state(ctx, st)
+        lam, _, _, _, _ = U.usbs_nystrom_round(ctx, want_u=False, want_signs=False)
         costs, scores, perms, best = U.usbs_qap_round(ctx, W, D)
-    assert list(perms[best]) == list(perm)
-    assert costs[best] == qap_cost(W, D, Pi)
+    # the leading column of U is v / |v|; the others span directions X_Pi does not have
+    # (their eigenvalues are round-off), and any of them may round to a cheaper permutation
+    k = int(np.argmax(lam))
+    assert lam[k] > 1e3 * np.max(np.abs(np.delete(lam, k)))
+    assert list(perms[k]) == list(perm)
+    assert costs[k] == qap_cost(W, D, Pi)
+    assert scores[k] == pytest.approx(NQ / np.linalg.norm(v), rel=1e-5)
+    assert best == int(np.argmin(costs)) and costs[best] <= costs[k]
