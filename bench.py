@@ -669,9 +669,10 @@ def run_c3(args, world, rank, local, pg):
 
 def run_sweep(args, world, rank, local, pg):
     """k_c / k_p grid (the paper's App. F parameter sweeps, on synthetic graphs): cold-start
-    solves to both gates <= 1e-3 in mixed precision, one per (graph, k_c, k_p), and for one
-    setting the model value by the App. B.1 IPM against its closed form.  Reports iterations,
-    seconds and the objective of each."""
+    solves to both gates <= 1e-3 in mixed precision, one per (graph, k_c, k_p) at --rho, for
+    one setting the model value by the App. B.1 IPM against its closed form, and (k_c, k_p) =
+    (8, 0) and (7, 1) at each rho of --sweep-rhos.  Reports iterations, seconds and the
+    objective of each."""
     import torch
     from paper_2312_11801_gb300 import build as B
     B.build()
@@ -680,21 +681,23 @@ def run_sweep(args, world, rank, local, pg):
     torch.cuda.set_device(local)
     graphs = {"er2000_d6": I.maxcut_er(2000, 6.0, 7), "rgg1000_d10": I.maxcut_rgg(1000, 10.0, seed=7)}
     grid = [(8, 0), (7, 1), (6, 2), (5, 3), (4, 0), (4, 2), (2, 1)]
+    rhos = [float(x) for x in args.sweep_rhos.split(",") if x.strip()]
+    runs = [(kc, kp, args.rho, mv) for (kc, kp) in grid for mv in ((0, 1) if (kc, kp) == (6, 2) else (0,))]
+    runs += [(kc, kp, rho, 0) for rho in rhos if rho != args.rho for (kc, kp) in ((8, 0), (7, 1))]
     rows = []
     t_all = time.perf_counter()
     for gname, prob in graphs.items():
-        for (kc, kp) in grid:
-            for mv in ((0, 1) if (kc, kp) == (6, 2) else (0,)):
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                with U.usbs_create(prob, precision=U.PRECISION_MIXED, k_c=kc, k_p=kp, rho=args.rho,
-                                   max_iters=min(args.max_iters, 1500), model_value_ipm=mv) as c:
-                    r = U.usbs_solve(c, tol=TOL)
-                torch.cuda.synchronize()
-                rows.append({"graph": gname, "k_c": kc, "k_p": kp, "model_value": "ipm" if mv else "closed",
-                             "iters": r["iters"], "converged": bool(r["converged"]),
-                             "seconds": time.perf_counter() - t0, "objective": r["last"]["objective"],
-                             "relgap": r["last"]["relgap"], "relinf": r["last"]["relinf"]})
+        for (kc, kp, rho, mv) in runs:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with U.usbs_create(prob, precision=U.PRECISION_MIXED, k_c=kc, k_p=kp, rho=rho,
+                               max_iters=min(args.max_iters, 1500), model_value_ipm=mv) as c:
+                r = U.usbs_solve(c, tol=TOL)
+            torch.cuda.synchronize()
+            rows.append({"graph": gname, "k_c": kc, "k_p": kp, "rho": rho, "model_value": "ipm" if mv else "closed",
+                         "iters": r["iters"], "converged": bool(r["converged"]),
+                         "seconds": time.perf_counter() - t0, "objective": r["last"]["objective"],
+                         "relgap": r["last"]["relgap"], "relinf": r["last"]["relinf"]})
     elapsed = max_over_ranks(pg, time.perf_counter() - t_all)
     conv = sum(r["converged"] for r in rows)
     line = {
@@ -761,7 +764,8 @@ def main():
     ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "batched", "serve", "sweep"])
     ap.add_argument("--c3-n", type=int, default=65536)
     ap.add_argument("--c3-rho", type=float, default=0.01)
-    ap.add_argument("--rho", type=float, default=0.1, help="rho of the batched and served workloads")
+    ap.add_argument("--rho", type=float, default=0.03, help="rho of the batched, served and sweep workloads")
+    ap.add_argument("--sweep-rhos", default="0.1,0.01", help="further rho values of the sweep, for (8, 0) and (7, 1)")
     ap.add_argument("--k-c", type=int, default=8, help="k_c of the batched and served workloads")
     ap.add_argument("--k-p", type=int, default=0, help="k_p of the batched and served workloads")
     ap.add_argument("--batch-count", type=int, default=512)

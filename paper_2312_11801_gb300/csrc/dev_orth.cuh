@@ -1,5 +1,5 @@
-// Device bodies of the block Gram-Schmidt kernels, staged through shared memory with
-// cp.async (double-buffered tiles of TR rows).  A body takes its CTA index and CTA count
+// Device bodies of the block Gram-Schmidt kernels, staged through shared memory by bulk
+// asynchronous copies (a pipeline of ns tiles of TR rows, 2 <= ns <= NSMAX).  A body takes its CTA index and CTA count
 // as arguments: the __global__ kernels in orth.cu pass blockIdx.x and gridDim.x, and the
 // batched solver calls a body with (0, 1), one CTA walking every tile.
 #pragma once
@@ -102,15 +102,33 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
       : "memory");
 }
 
-// Two stage barriers, initialised by thread 0 and published by the barrier that follows.
-__device__ __forceinline__ void tiles_begin(uint64_t* bar) {
+// The tile pipeline has ns stages (2 <= ns <= NSMAX), each with its own barrier: iteration
+// k of a CTA's tile loop (tile cta + k ncta) reads stage k % ns and waits for phase k / ns
+// of barrier k % ns; at its top it issues the copies of iteration k + ns - 1 into the stage
+// that iteration k - 1 released at its closing __syncthreads.  ns - 1 tiles are thus in
+// flight while one is used: deeper pipelines keep more bytes in flight when the stages are
+// small (few basis blocks).
+constexpr int NSMAX = 4;
+
+// Stage barriers, initialised by thread 0 and published by the barrier that follows.
+__device__ __forceinline__ void tiles_begin(uint64_t* bar, int ns) {
   if (threadIdx.x == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    for (int s = 0; s < ns; ++s) mbar_init(&bar[s], 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   __syncthreads();
 }
+
+// Stage indices of the loop: s (the stage read in this iteration) with its barrier phase,
+// and sl (the stage the copies issued in this iteration go to, (s + ns - 1) % ns).
+struct TileRing {
+  int ns, s, ph, sl;
+  __device__ explicit TileRing(int ns_) : ns(ns_), s(0), ph(0), sl(ns_ - 1) {}
+  __device__ void next() {
+    if (++s == ns) { s = 0; ph ^= 1; }
+    if (++sl == ns) sl = 0;
+  }
+};
 
 // Stage rows [row0, row0 + TR) of blocks 0..nq-1 of Q and of W (if given, after them).
 template <typename T, int TR>
@@ -161,18 +179,17 @@ __device__ __forceinline__ bool tile_wait_cta(uint64_t* bar, unsigned parity, in
   return ok;
 }
 
-// After the tile loop: on an abort, wait (bounded) for copies that may still be landing in
-// either stage, then release the barriers.
-__device__ __forceinline__ void tiles_end(uint64_t* bar, bool aborted, int it_abort, int left_after, int* status) {
-  (void)status;
-  if (aborted) {
-    tile_wait(&bar[it_abort & 1], (it_abort >> 1) & 1, nullptr);
-    if (left_after) tile_wait(&bar[(it_abort + 1) & 1], ((it_abort + 1) >> 1) & 1, nullptr);
+// After the tile loop: on an abort at iteration it_abort (-1: none), wait (bounded) for the
+// copies that may still be landing, those of iterations it_abort .. it_abort + ns - 1 whose
+// tiles exist, then release the barriers.
+__device__ __forceinline__ void tiles_end(uint64_t* bar, int ns, int it_abort, int cta, int ncta, int ntiles) {
+  if (it_abort >= 0) {
+    for (int k = it_abort; k < it_abort + ns; ++k)
+      if ((int64_t)cta + (int64_t)k * ncta < ntiles) tile_wait(&bar[k % ns], (unsigned)(k / ns) & 1u, nullptr);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    mbar_inval(&bar[0]);
-    mbar_inval(&bar[1]);
+    for (int s = 0; s < ns; ++s) mbar_inval(&bar[s]);
   }
 }
 
@@ -285,7 +302,7 @@ __device__ __forceinline__ void tc_reduce_xty(const float (&acc)[MAXP][4], int n
 
 // H = Q^T W for nb <= 8 blocks
 __device__ __forceinline__ void tc_tproj(const int cta, const int ncta, int n, const float* Q, size_t bstride,
-                                         int nb, const float* W, double* partials, int* status) {
+                                         int nb, const float* W, double* partials, int* status, int ns = 2) {
   constexpr int TR = 128, BS = BlockStride<float>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* stages = reinterpret_cast<float*>(smem_raw);
@@ -297,26 +314,25 @@ __device__ __forceinline__ void tc_tproj(const int cta, const int ncta, int n, c
 #pragma unroll
     for (int u = 0; u < 4; ++u) acc[p][u] = accb[p][u] = 0.f;
   const int ntiles = (n + TR - 1) / TR;
-  int tile = cta;
-  __shared__ uint64_t tbar[2];
-  tiles_begin(tbar);
-  bool aborted = false;
-  int it_abort = 0, left_after = 0;
-  if (tile < ntiles) tile_load<float, TR>(stages, Q, bstride, nb, W, n, tile * TR, &tbar[0]);
-  for (int it = 0; tile < ntiles; ++it, tile += ncta) {
-    const int next = tile + ncta;
-    if (next < ntiles) tile_load<float, TR>(stages + ((it + 1) & 1) * sstride, Q, bstride, nb, W, n, next * TR, &tbar[(it + 1) & 1]);
-    if (!tile_wait_cta(&tbar[it & 1], (it >> 1) & 1, status)) {
-      aborted = true;
+  __shared__ uint64_t tbar[NSMAX];
+  tiles_begin(tbar, ns);
+  for (int k = 0; k < ns - 1; ++k)
+    if (cta + k * ncta < ntiles)
+      tile_load<float, TR>(stages + k * sstride, Q, bstride, nb, W, n, (cta + k * ncta) * TR, &tbar[k]);
+  int it_abort = -1;
+  TileRing rg(ns);
+  for (int it = 0, tile = cta; tile < ntiles; ++it, tile += ncta, rg.next()) {
+    const int ahead = tile + (ns - 1) * ncta;
+    if (ahead < ntiles) tile_load<float, TR>(stages + rg.sl * sstride, Q, bstride, nb, W, n, ahead * TR, &tbar[rg.sl]);
+    if (!tile_wait_cta(&tbar[rg.s], rg.ph, status)) {
       it_abort = it;
-      left_after = next < ntiles;
       break;
     }
-    const float* st = stages + (it & 1) * sstride;
+    const float* st = stages + rg.s * sstride;
     tc_accum_xty<4>(st, nb, st + (size_t)nb * BS, warp, g, t, acc, accb);
     __syncthreads();
   }
-  tiles_end(tbar, aborted, it_abort, left_after, status);
+  tiles_end(tbar, ns, it_abort, cta, ncta, ntiles);
   __syncthreads();
 #pragma unroll
   for (int p = 0; p < 4; ++p)
@@ -329,12 +345,12 @@ __device__ __forceinline__ void tc_tproj(const int cta, const int ncta, int n, c
 // X = W - Q H (W overwritten, in shared memory and in global memory); then H2 = Q^T X and
 // G = X^T X.  H in Hs (nb x 64, FP32).
 __device__ __forceinline__ void tc_tupdate(const int cta, const int ncta, int n, const float* Q, size_t bstride,
-                                           int nb, float* W, const double* Hred, double* partials, int* status) {
+                                           int nb, float* W, const double* Hred, double* partials, int* status, int ns = 2) {
   constexpr int TR = 128, BS = BlockStride<float>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* stages = reinterpret_cast<float*>(smem_raw);
   const int sstride = (nb + 1) * BS;
-  float* Hs = stages + 2 * sstride;
+  float* Hs = stages + ns * sstride;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   for (int u = threadIdx.x; u < nb * 64; u += blockDim.x) Hs[u] = (float)Hred[u];
   __syncthreads();
@@ -349,22 +365,21 @@ __device__ __forceinline__ void tc_tupdate(const int cta, const int ncta, int n,
 #pragma unroll
     for (int u = 0; u < 4; ++u) acc[p][u] = accb[p][u] = 0.f;
   const int ntiles = (n + TR - 1) / TR;
-  int tile = cta;
-  __shared__ uint64_t tbar[2];
-  tiles_begin(tbar);
-  bool aborted = false;
-  int it_abort = 0, left_after = 0;
-  if (tile < ntiles) tile_load<float, TR>(stages, Q, bstride, nb, W, n, tile * TR, &tbar[0]);
-  for (int it = 0; tile < ntiles; ++it, tile += ncta) {
-    const int next = tile + ncta;
-    if (next < ntiles) tile_load<float, TR>(stages + ((it + 1) & 1) * sstride, Q, bstride, nb, W, n, next * TR, &tbar[(it + 1) & 1]);
-    if (!tile_wait_cta(&tbar[it & 1], (it >> 1) & 1, status)) {
-      aborted = true;
+  __shared__ uint64_t tbar[NSMAX];
+  tiles_begin(tbar, ns);
+  for (int k = 0; k < ns - 1; ++k)
+    if (cta + k * ncta < ntiles)
+      tile_load<float, TR>(stages + k * sstride, Q, bstride, nb, W, n, (cta + k * ncta) * TR, &tbar[k]);
+  int it_abort = -1;
+  TileRing rg(ns);
+  for (int it = 0, tile = cta; tile < ntiles; ++it, tile += ncta, rg.next()) {
+    const int ahead = tile + (ns - 1) * ncta;
+    if (ahead < ntiles) tile_load<float, TR>(stages + rg.sl * sstride, Q, bstride, nb, W, n, ahead * TR, &tbar[rg.sl]);
+    if (!tile_wait_cta(&tbar[rg.s], rg.ph, status)) {
       it_abort = it;
-      left_after = next < ntiles;
       break;
     }
-    float* st = stages + (it & 1) * sstride;
+    float* st = stages + rg.s * sstride;
     float* Xs = st + (size_t)nb * BS;
     // phase 1: rows 16 warp .. 16 warp + 15 of X = W - Q H
     {
@@ -395,7 +410,7 @@ __device__ __forceinline__ void tc_tupdate(const int cta, const int ncta, int n,
     tc_accum_xty<5>(st, nb + 1, Xs, warp, g, t, acc, accb);
     __syncthreads();
   }
-  tiles_end(tbar, aborted, it_abort, left_after, status);
+  tiles_end(tbar, ns, it_abort, cta, ncta, ntiles);
   __syncthreads();
 #pragma unroll
   for (int p = 0; p < 5; ++p)
@@ -408,12 +423,12 @@ __device__ __forceinline__ void tc_tupdate(const int cta, const int ncta, int n,
 // out = (W - Q H2) R^-1, deficient columns replaced (1: random, 2: zero)
 __device__ __forceinline__ void tc_tfinalize(const int cta, const int ncta, int n, const float* Q, size_t bstride,
                                              int nb, const float* W, const double* H2red, const DevLanczos* lz,
-                                             float* out, uint64_t seed, int* status) {
+                                             float* out, uint64_t seed, int* status, int ns = 2) {
   constexpr int TR = 128, BS = BlockStride<float>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* stages = reinterpret_cast<float*>(smem_raw);
   const int sstride = (nb + 1) * BS;
-  float* Hs = stages + 2 * sstride;
+  float* Hs = stages + ns * sstride;
   float* Ri = Hs + 8 * 64;
   __shared__ int dfc[8];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
@@ -428,22 +443,21 @@ __device__ __forceinline__ void tc_tfinalize(const int cta, const int ncta, int 
   for (int b = 0; b < 8; ++b)
     hb[b] = (b < nb) ? split_b(Hs[b * 64 + t * 8 + g], Hs[b * 64 + (t + 4) * 8 + g]) : SplitB{0u, 0u, 0u, 0u};
   const int ntiles = (n + TR - 1) / TR;
-  int tile = cta;
-  __shared__ uint64_t tbar[2];
-  tiles_begin(tbar);
-  bool aborted = false;
-  int it_abort = 0, left_after = 0;
-  if (tile < ntiles) tile_load<float, TR>(stages, Q, bstride, nb, W, n, tile * TR, &tbar[0]);
-  for (int it = 0; tile < ntiles; ++it, tile += ncta) {
-    const int next = tile + ncta;
-    if (next < ntiles) tile_load<float, TR>(stages + ((it + 1) & 1) * sstride, Q, bstride, nb, W, n, next * TR, &tbar[(it + 1) & 1]);
-    if (!tile_wait_cta(&tbar[it & 1], (it >> 1) & 1, status)) {
-      aborted = true;
+  __shared__ uint64_t tbar[NSMAX];
+  tiles_begin(tbar, ns);
+  for (int k = 0; k < ns - 1; ++k)
+    if (cta + k * ncta < ntiles)
+      tile_load<float, TR>(stages + k * sstride, Q, bstride, nb, W, n, (cta + k * ncta) * TR, &tbar[k]);
+  int it_abort = -1;
+  TileRing rg(ns);
+  for (int it = 0, tile = cta; tile < ntiles; ++it, tile += ncta, rg.next()) {
+    const int ahead = tile + (ns - 1) * ncta;
+    if (ahead < ntiles) tile_load<float, TR>(stages + rg.sl * sstride, Q, bstride, nb, W, n, ahead * TR, &tbar[rg.sl]);
+    if (!tile_wait_cta(&tbar[rg.s], rg.ph, status)) {
       it_abort = it;
-      left_after = next < ntiles;
       break;
     }
-    float* st = stages + (it & 1) * sstride;
+    float* st = stages + rg.s * sstride;
     float* Xs = st + (size_t)nb * BS;
     const int rb = 16 * warp;
     float d[4] = {0.f, 0.f, 0.f, 0.f}, e0[4] = {0.f, 0.f, 0.f, 0.f};
@@ -479,20 +493,20 @@ __device__ __forceinline__ void tc_tfinalize(const int cta, const int ncta, int 
     if (row1 < n) *reinterpret_cast<float2*>(out + (size_t)8 * row1 + 2 * t) = make_float2(o[2], o[3]);
     __syncthreads();
   }
-  tiles_end(tbar, aborted, it_abort, left_after, status);
+  tiles_end(tbar, ns, it_abort, cta, ncta, ntiles);
 }
 
 // out[o] = Q[:, :J] Y[:, 8o : 8o + 8] for o < nout <= 4; the residual block copied to
 // out[resid_slot] when resid is given.  Ys: J x 8 nout split pairs in shared memory.
 __device__ __forceinline__ void tc_trestart(const int cta, const int ncta, int n, const float* Q, size_t bstride,
                                             int nbk, int nout, const double* Y, float* out, size_t ostride,
-                                            const float* resid, int resid_slot, int* status) {
+                                            const float* resid, int resid_slot, int* status, int ns = 2) {
   constexpr int TR = 128, BS = BlockStride<float>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* stages = reinterpret_cast<float*>(smem_raw);
   const int sstride = nbk * BS;
   // Y split once per launch into TF32 high and low parts: (hi, lo) pairs, J x 8 nout
-  uint2* Ys = reinterpret_cast<uint2*>(stages + 2 * sstride);
+  uint2* Ys = reinterpret_cast<uint2*>(stages + ns * sstride);
   const int J = nbk * 8, ncol = nout * 8;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
   for (int u = tid; u < J * ncol; u += blockDim.x) {
@@ -501,22 +515,21 @@ __device__ __forceinline__ void tc_trestart(const int cta, const int ncta, int n
     Ys[u] = make_uint2(hi, lo);
   }
   const int ntiles = (n + TR - 1) / TR;
-  int tile = cta;
-  __shared__ uint64_t tbar[2];
-  tiles_begin(tbar);
-  bool aborted = false;
-  int it_abort = 0, left_after = 0;
-  if (tile < ntiles) tile_load<float, TR>(stages, Q, bstride, nbk, nullptr, n, tile * TR, &tbar[0]);
-  for (int it = 0; tile < ntiles; ++it, tile += ncta) {
-    const int next = tile + ncta;
-    if (next < ntiles) tile_load<float, TR>(stages + ((it + 1) & 1) * sstride, Q, bstride, nbk, nullptr, n, next * TR, &tbar[(it + 1) & 1]);
-    if (!tile_wait_cta(&tbar[it & 1], (it >> 1) & 1, status)) {
-      aborted = true;
+  __shared__ uint64_t tbar[NSMAX];
+  tiles_begin(tbar, ns);
+  for (int k = 0; k < ns - 1; ++k)
+    if (cta + k * ncta < ntiles)
+      tile_load<float, TR>(stages + k * sstride, Q, bstride, nbk, nullptr, n, (cta + k * ncta) * TR, &tbar[k]);
+  int it_abort = -1;
+  TileRing rg(ns);
+  for (int it = 0, tile = cta; tile < ntiles; ++it, tile += ncta, rg.next()) {
+    const int ahead = tile + (ns - 1) * ncta;
+    if (ahead < ntiles) tile_load<float, TR>(stages + rg.sl * sstride, Q, bstride, nbk, nullptr, n, ahead * TR, &tbar[rg.sl]);
+    if (!tile_wait_cta(&tbar[rg.s], rg.ph, status)) {
       it_abort = it;
-      left_after = next < ntiles;
       break;
     }
-    const float* st = stages + (it & 1) * sstride;
+    const float* st = stages + rg.s * sstride;
     const int rb = 16 * warp;
     // small terms in d, large terms in e: independent accumulators per output block
     float d[4][4], e[4][4];
@@ -561,7 +574,7 @@ __device__ __forceinline__ void tc_trestart(const int cta, const int ncta, int n
     }
     __syncthreads();
   }
-  tiles_end(tbar, aborted, it_abort, left_after, status);
+  tiles_end(tbar, ns, it_abort, cta, ncta, ntiles);
 }
 
 // ---- H = Q^T W --------------------------------------------------------------------------
@@ -601,10 +614,10 @@ __device__ __forceinline__ double sum_slots(const double* red, int nitems, int n
 template <typename T>
 __device__ __forceinline__ void k_tproj_dev(const int cta, const int ncta, int n, const T* USBS_RESTRICT Q, size_t bstride, int nb,
                                                const T* USBS_RESTRICT W, double* USBS_RESTRICT partials,
-                                               const int* USBS_RESTRICT mask, int* status) {
+                                               const int* USBS_RESTRICT mask, int* status, int ns = 2) {
   if constexpr (sizeof(T) == 4) {
     if (mask && *mask == 0) return;
-    tc_tproj(cta, ncta, n, Q, bstride, nb, W, partials, status);
+    tc_tproj(cta, ncta, n, Q, bstride, nb, W, partials, status, ns);
     return;
   }
   if (mask && *mask == 0) return;
@@ -621,29 +634,28 @@ __device__ __forceinline__ void k_tproj_dev(const int cta, const int ncta, int n
 #pragma unroll
   for (int u = 0; u < 16; ++u) acc[u] = (T)0;
   const int ntiles = (n + TR - 1) / TR;
-  int tile = cta;
-  __shared__ uint64_t tbar[2];
-  tiles_begin(tbar);
-  bool aborted = false;
-  int it_abort = 0, left_after = 0;
-  if (tile < ntiles) tile_load<T, TR>(stages, Q, bstride, nb, W, n, tile * TR, &tbar[0]);
-  for (int it = 0; tile < ntiles; ++it, tile += ncta) {
-    const int next = tile + ncta;
-    if (next < ntiles) tile_load<T, TR>(stages + ((it + 1) & 1) * sstride, Q, bstride, nb, W, n, next * TR, &tbar[(it + 1) & 1]);
-    if (!tile_wait_cta(&tbar[it & 1], (it >> 1) & 1, status)) {
-      aborted = true;
+  __shared__ uint64_t tbar[NSMAX];
+  tiles_begin(tbar, ns);
+  for (int k = 0; k < ns - 1; ++k)
+    if (cta + k * ncta < ntiles)
+      tile_load<T, TR>(stages + k * sstride, Q, bstride, nb, W, n, (cta + k * ncta) * TR, &tbar[k]);
+  int it_abort = -1;
+  TileRing rg(ns);
+  for (int it = 0, tile = cta; tile < ntiles; ++it, tile += ncta, rg.next()) {
+    const int ahead = tile + (ns - 1) * ncta;
+    if (ahead < ntiles) tile_load<T, TR>(stages + rg.sl * sstride, Q, bstride, nb, W, n, ahead * TR, &tbar[rg.sl]);
+    if (!tile_wait_cta(&tbar[rg.s], rg.ph, status)) {
       it_abort = it;
-      left_after = next < ntiles;
       break;
     }
-    const T* st = stages + (it & 1) * sstride;
+    const T* st = stages + rg.s * sstride;
     if (active) {
       const int b = item >> 2, a0 = 2 * (item & 3);
       accum_pair<T>(st + (size_t)b * BlockStride<T>::value + a0, st + (size_t)nb * BlockStride<T>::value, grp + 8 * sub, 8 * nsub, acc);
     }
     __syncthreads();
   }
-  tiles_end(tbar, aborted, it_abort, left_after, status);
+  tiles_end(tbar, ns, it_abort, cta, ncta, ntiles);
   __syncthreads();
   double* red = reinterpret_cast<double*>(smem_raw);     // 8 warps x 32 slots x 16
   if (active) {
@@ -663,10 +675,10 @@ template <typename T>
 __device__ __forceinline__ void k_tupdate_dev(const int cta, const int ncta, int n, const T* USBS_RESTRICT Q, size_t bstride, int nb,
                                                  T* USBS_RESTRICT W, const double* USBS_RESTRICT Hred,
                                                  double* USBS_RESTRICT partials,
-                                                 const int* USBS_RESTRICT mask, int* status) {
+                                                 const int* USBS_RESTRICT mask, int* status, int ns = 2) {
   if constexpr (sizeof(T) == 4) {
     if (mask && *mask == 0) return;
-    tc_tupdate(cta, ncta, n, Q, bstride, nb, W, Hred, partials, status);
+    tc_tupdate(cta, ncta, n, Q, bstride, nb, W, Hred, partials, status, ns);
     return;
   }
   if (mask && *mask == 0) return;
@@ -674,7 +686,7 @@ __device__ __forceinline__ void k_tupdate_dev(const int cta, const int ncta, int
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* stages = reinterpret_cast<T*>(smem_raw);
   const int sstride = (nb + 1) * BlockStride<T>::value;
-  T* Hs = stages + 2 * sstride;                             // nb x 8 x 8
+  T* Hs = stages + ns * sstride;                             // nb x 8 x 8
   const int tid = threadIdx.x, grp = tid >> 5, slot = tid & 31;
   for (int t = tid; t < nb * 64; t += blockDim.x) Hs[t] = (T)Hred[t];
   const int nitems = 4 * (nb + 1);                          // item b == nb: the Gram matrix
@@ -688,22 +700,21 @@ __device__ __forceinline__ void k_tupdate_dev(const int cta, const int ncta, int
 #pragma unroll
     for (int v = 0; v < 16; ++v) acc[u][v] = (T)0;
   const int ntiles = (n + TR - 1) / TR;
-  int tile = cta;
-  __shared__ uint64_t tbar[2];
-  tiles_begin(tbar);
-  bool aborted = false;
-  int it_abort = 0, left_after = 0;
-  if (tile < ntiles) tile_load<T, TR>(stages, Q, bstride, nb, W, n, tile * TR, &tbar[0]);
-  for (int it = 0; tile < ntiles; ++it, tile += ncta) {
-    const int next = tile + ncta;
-    if (next < ntiles) tile_load<T, TR>(stages + ((it + 1) & 1) * sstride, Q, bstride, nb, W, n, next * TR, &tbar[(it + 1) & 1]);
-    if (!tile_wait_cta(&tbar[it & 1], (it >> 1) & 1, status)) {
-      aborted = true;
+  __shared__ uint64_t tbar[NSMAX];
+  tiles_begin(tbar, ns);
+  for (int k = 0; k < ns - 1; ++k)
+    if (cta + k * ncta < ntiles)
+      tile_load<T, TR>(stages + k * sstride, Q, bstride, nb, W, n, (cta + k * ncta) * TR, &tbar[k]);
+  int it_abort = -1;
+  TileRing rg(ns);
+  for (int it = 0, tile = cta; tile < ntiles; ++it, tile += ncta, rg.next()) {
+    const int ahead = tile + (ns - 1) * ncta;
+    if (ahead < ntiles) tile_load<T, TR>(stages + rg.sl * sstride, Q, bstride, nb, W, n, ahead * TR, &tbar[rg.sl]);
+    if (!tile_wait_cta(&tbar[rg.s], rg.ph, status)) {
       it_abort = it;
-      left_after = next < ntiles;
       break;
     }
-    T* st = stages + (it & 1) * sstride;
+    T* st = stages + rg.s * sstride;
     T* Xs = st + (size_t)nb * BlockStride<T>::value;                               // W tile, overwritten by X
     // phase 1: X = W - Q H, 4 columns per thread
     for (int p = tid; p < TR * 2; p += blockDim.x) {
@@ -742,7 +753,7 @@ __device__ __forceinline__ void k_tupdate_dev(const int cta, const int ncta, int
     }
     __syncthreads();
   }
-  tiles_end(tbar, aborted, it_abort, left_after, status);
+  tiles_end(tbar, ns, it_abort, cta, ncta, ntiles);
   __syncthreads();
   double* red = reinterpret_cast<double*>(smem_raw);     // 8 warps x nslot x 16
 #pragma unroll
@@ -768,10 +779,10 @@ template <typename T>
 __device__ __forceinline__ void k_tfinalize_dev(const int cta, const int ncta, int n, const T* USBS_RESTRICT Q, size_t bstride,
                                                    int nb, const T* W, const double* USBS_RESTRICT H2red,
                                                    const DevLanczos* USBS_RESTRICT lz, T* out,
-                                                   const int* USBS_RESTRICT mask, uint64_t seed, int* status) {
+                                                   const int* USBS_RESTRICT mask, uint64_t seed, int* status, int ns = 2) {
   if constexpr (sizeof(T) == 4) {
     if (mask && *mask == 0) return;
-    tc_tfinalize(cta, ncta, n, Q, bstride, nb, W, H2red, lz, out, seed, status);
+    tc_tfinalize(cta, ncta, n, Q, bstride, nb, W, H2red, lz, out, seed, status, ns);
     return;
   }
   if (mask && *mask == 0) return;
@@ -779,7 +790,7 @@ __device__ __forceinline__ void k_tfinalize_dev(const int cta, const int ncta, i
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* stages = reinterpret_cast<T*>(smem_raw);
   const int sstride = (nb + 1) * BlockStride<T>::value;
-  T* Hs = stages + 2 * sstride;
+  T* Hs = stages + ns * sstride;
   T* Ri = Hs + 8 * 64;
   __shared__ int dfc[8];
   const int tid = threadIdx.x;
@@ -787,22 +798,21 @@ __device__ __forceinline__ void k_tfinalize_dev(const int cta, const int ncta, i
   if (tid < 64) Ri[tid] = (T)lz->Rinv[tid];
   if (tid < 8) dfc[tid] = lz->dcol[tid];
   const int ntiles = (n + TR - 1) / TR;
-  int tile = cta;
-  __shared__ uint64_t tbar[2];
-  tiles_begin(tbar);
-  bool aborted = false;
-  int it_abort = 0, left_after = 0;
-  if (tile < ntiles) tile_load<T, TR>(stages, Q, bstride, nb, W, n, tile * TR, &tbar[0]);
-  for (int it = 0; tile < ntiles; ++it, tile += ncta) {
-    const int next = tile + ncta;
-    if (next < ntiles) tile_load<T, TR>(stages + ((it + 1) & 1) * sstride, Q, bstride, nb, W, n, next * TR, &tbar[(it + 1) & 1]);
-    if (!tile_wait_cta(&tbar[it & 1], (it >> 1) & 1, status)) {
-      aborted = true;
+  __shared__ uint64_t tbar[NSMAX];
+  tiles_begin(tbar, ns);
+  for (int k = 0; k < ns - 1; ++k)
+    if (cta + k * ncta < ntiles)
+      tile_load<T, TR>(stages + k * sstride, Q, bstride, nb, W, n, (cta + k * ncta) * TR, &tbar[k]);
+  int it_abort = -1;
+  TileRing rg(ns);
+  for (int it = 0, tile = cta; tile < ntiles; ++it, tile += ncta, rg.next()) {
+    const int ahead = tile + (ns - 1) * ncta;
+    if (ahead < ntiles) tile_load<T, TR>(stages + rg.sl * sstride, Q, bstride, nb, W, n, ahead * TR, &tbar[rg.sl]);
+    if (!tile_wait_cta(&tbar[rg.s], rg.ph, status)) {
       it_abort = it;
-      left_after = next < ntiles;
       break;
     }
-    T* st = stages + (it & 1) * sstride;
+    T* st = stages + rg.s * sstride;
     T* Xs = st + (size_t)nb * BlockStride<T>::value;
     for (int p = tid; p < TR * 2; p += blockDim.x) {
       const int r = p >> 1, c0 = 4 * (p & 1);
@@ -842,7 +852,7 @@ __device__ __forceinline__ void k_tfinalize_dev(const int cta, const int ncta, i
     }
     __syncthreads();
   }
-  tiles_end(tbar, aborted, it_abort, left_after, status);
+  tiles_end(tbar, ns, it_abort, cta, ncta, ntiles);
 }
 
 
@@ -853,36 +863,35 @@ template <typename T>
 __device__ __forceinline__ void k_trestart_dev(const int cta, const int ncta, int n, const T* USBS_RESTRICT Q, size_t bstride, int nbk,
                                                   int nout, const double* USBS_RESTRICT Y,
                                                   T* USBS_RESTRICT out, size_t ostride,
-                                                  const T* USBS_RESTRICT resid, int resid_slot, int* status) {
+                                                  const T* USBS_RESTRICT resid, int resid_slot, int* status, int ns = 2) {
   if constexpr (sizeof(T) == 4) {
-    tc_trestart(cta, ncta, n, Q, bstride, nbk, nout, Y, out, ostride, resid, resid_slot, status);
+    tc_trestart(cta, ncta, n, Q, bstride, nbk, nout, Y, out, ostride, resid, resid_slot, status, ns);
     return;
   }
   constexpr int TR = TileRows<T>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* stages = reinterpret_cast<T*>(smem_raw);
   const int sstride = nbk * BlockStride<T>::value;
-  T* Ys = stages + 2 * sstride;                       // J x ncol
+  T* Ys = stages + ns * sstride;                       // J x ncol
   const int J = nbk * 8, ncol = nout * 8;
   const int tid = threadIdx.x;
   for (int t = tid; t < J * ncol; t += blockDim.x) Ys[t] = (T)Y[(t / ncol) * JMAX + (t % ncol)];
   const int ntiles = (n + TR - 1) / TR;
-  int tile = cta;
-  __shared__ uint64_t tbar[2];
-  tiles_begin(tbar);
-  bool aborted = false;
-  int it_abort = 0, left_after = 0;
-  if (tile < ntiles) tile_load<T, TR>(stages, Q, bstride, nbk, nullptr, n, tile * TR, &tbar[0]);
-  for (int it = 0; tile < ntiles; ++it, tile += ncta) {
-    const int next = tile + ncta;
-    if (next < ntiles) tile_load<T, TR>(stages + ((it + 1) & 1) * sstride, Q, bstride, nbk, nullptr, n, next * TR, &tbar[(it + 1) & 1]);
-    if (!tile_wait_cta(&tbar[it & 1], (it >> 1) & 1, status)) {
-      aborted = true;
+  __shared__ uint64_t tbar[NSMAX];
+  tiles_begin(tbar, ns);
+  for (int k = 0; k < ns - 1; ++k)
+    if (cta + k * ncta < ntiles)
+      tile_load<T, TR>(stages + k * sstride, Q, bstride, nbk, nullptr, n, (cta + k * ncta) * TR, &tbar[k]);
+  int it_abort = -1;
+  TileRing rg(ns);
+  for (int it = 0, tile = cta; tile < ntiles; ++it, tile += ncta, rg.next()) {
+    const int ahead = tile + (ns - 1) * ncta;
+    if (ahead < ntiles) tile_load<T, TR>(stages + rg.sl * sstride, Q, bstride, nbk, nullptr, n, ahead * TR, &tbar[rg.sl]);
+    if (!tile_wait_cta(&tbar[rg.s], rg.ph, status)) {
       it_abort = it;
-      left_after = next < ntiles;
       break;
     }
-    const T* st = stages + (it & 1) * sstride;
+    const T* st = stages + rg.s * sstride;
     // items (row pair, output block, column group): with nout < 4 the 8 columns of an
     // output block are split into 4 / nout groups so that every thread has work
     const int ngrp = nout >= 4 ? 1 : 4 / nout, ncols = 8 / ngrp;
@@ -929,7 +938,7 @@ __device__ __forceinline__ void k_trestart_dev(const int cta, const int ncta, in
     }
     __syncthreads();
   }
-  tiles_end(tbar, aborted, it_abort, left_after, status);
+  tiles_end(tbar, ns, it_abort, cta, ncta, ntiles);
 }
 
 }  // namespace

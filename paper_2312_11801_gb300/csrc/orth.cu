@@ -1,9 +1,10 @@
 // Block Gram-Schmidt kernels of the Lanczos step, staged through shared memory.
 //
 // A CTA walks tiles of TR consecutive rows.  For each tile it copies the rows of every
-// basis block Q_0..Q_{nb-1} and of the new block W into shared memory with cp.async
-// (16-byte chunks; in the block-major layout the tile of one block is TR * 8 contiguous
-// values), double-buffered so the next tile streams in while the current one is used.
+// basis block Q_0..Q_{nb-1} and of the new block W into shared memory with bulk
+// asynchronous copies (in the block-major layout the tile of one block is TR * 8
+// contiguous values), in a pipeline of 2 to 4 stages (as many as fit while two CTAs share
+// an SM), so that the next tiles stream in while the current one is used.
 // The arithmetic then runs from shared memory as small register-blocked GEMMs:
 //   proj     : H  += Q^T W                                   (first projection)
 //   update   : X = W - Q H (written back), H2 += Q^T X, G += X^T X   (second pass, Gram)
@@ -23,49 +24,66 @@ namespace {
 template <typename T>
 __global__ void __launch_bounds__(256, 2) k_tproj(int n, const T* __restrict__ Q, size_t bstride, int nb,
                                                const T* __restrict__ W, double* __restrict__ partials,
-                                               const int* __restrict__ mask, int* status) {
-  k_tproj_dev<T>(blockIdx.x, gridDim.x, n, Q, bstride, nb, W, partials, mask, status);
+                                               const int* __restrict__ mask, int* status, int ns) {
+  k_tproj_dev<T>(blockIdx.x, gridDim.x, n, Q, bstride, nb, W, partials, mask, status, ns);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256, 2) k_tupdate(int n, const T* __restrict__ Q, size_t bstride, int nb,
                                                  T* __restrict__ W, const double* __restrict__ Hred,
                                                  double* __restrict__ partials,
-                                                 const int* __restrict__ mask, int* status) {
-  k_tupdate_dev<T>(blockIdx.x, gridDim.x, n, Q, bstride, nb, W, Hred, partials, mask, status);
+                                                 const int* __restrict__ mask, int* status, int ns) {
+  k_tupdate_dev<T>(blockIdx.x, gridDim.x, n, Q, bstride, nb, W, Hred, partials, mask, status, ns);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256, 2) k_tfinalize(int n, const T* __restrict__ Q, size_t bstride,
                                                    int nb, const T* W, const double* __restrict__ H2red,
                                                    const DevLanczos* __restrict__ lz, T* out,
-                                                   const int* __restrict__ mask, uint64_t seed, int* status) {
-  k_tfinalize_dev<T>(blockIdx.x, gridDim.x, n, Q, bstride, nb, W, H2red, lz, out, mask, seed, status);
+                                                   const int* __restrict__ mask, uint64_t seed, int* status, int ns) {
+  k_tfinalize_dev<T>(blockIdx.x, gridDim.x, n, Q, bstride, nb, W, H2red, lz, out, mask, seed, status, ns);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256, 2) k_trestart(int n, const T* __restrict__ Q, size_t bstride, int nbk,
                                                   int nout, const double* __restrict__ Y,
                                                   T* __restrict__ out, size_t ostride,
-                                                  const T* __restrict__ resid, int resid_slot, int* status) {
-  k_trestart_dev<T>(blockIdx.x, gridDim.x, n, Q, bstride, nbk, nout, Y, out, ostride, resid, resid_slot, status);
+                                                  const T* __restrict__ resid, int resid_slot, int* status, int ns) {
+  k_trestart_dev<T>(blockIdx.x, gridDim.x, n, Q, bstride, nbk, nout, Y, out, ostride, resid, resid_slot, status, ns);
 }
 
+// Dynamic shared memory of one CTA: a budget under which two CTAs still share an SM
+// (228 KB per SM, 1 KB of it reserved per CTA), so the pipeline depth never costs occupancy.
+constexpr size_t PIPE_BUDGET = 110 * 1024;
+
+// Stages of the tile pipeline for one launch: as many as fit the budget, 2 to NSMAX.
+static int pipe_stages(size_t stage_bytes, size_t fixed_bytes) {
+  int ns = 2;
+  while (ns < NSMAX && (size_t)(ns + 1) * stage_bytes + fixed_bytes <= PIPE_BUDGET) ++ns;
+  return ns;
+}
+
+// bytes of one stage of nb + 1 staged blocks, and the pipeline depth with `extra` values after it
 template <typename T>
-size_t tile_smem(int nb, int extra) {
-  return sizeof(T) * (2 * (size_t)(nb + 1) * BlockStride<T>::value + extra);
+size_t stage_bytes(int nblk) { return sizeof(T) * (size_t)nblk * BlockStride<T>::value; }
+template <typename T>
+int tile_stages(int nb, int extra) { return pipe_stages(stage_bytes<T>(nb + 1), sizeof(T) * (size_t)extra); }
+template <typename T>
+size_t tile_smem(int nb, int extra, int ns) {
+  return (size_t)ns * stage_bytes<T>(nb + 1) + sizeof(T) * (size_t)extra;
 }
 
 template <typename T>
 void set_attrs() {
   static std::once_flag once;
   std::call_once(once, [] {
-    const int mx = (int)tile_smem<T>(8, 8 * 64 + 64);
+    // the largest launch: two stages of nine blocks (nb = 8) or the budget
+    const int mx = (int)std::max(tile_smem<T>(8, 8 * 64 + 64, 2), PIPE_BUDGET);
     cudaFuncSetAttribute(k_tproj<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_tupdate<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_tfinalize<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_trestart<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(sizeof(T) * (2 * (size_t)8 * BlockStride<T>::value) + 8 * JMAX * 32));
+                         (int)std::max(2 * stage_bytes<T>(8) + 8 * JMAX * 32, PIPE_BUDGET));
   });
 }
 
@@ -120,10 +138,11 @@ int Orth<T>::proj(Ctx* c, const void* Qb, int nb, const void* W, const int* mask
   }
   set_attrs<T>();
   // the epilogue reuses the stage buffers for its warp partials
-  const size_t sm = std::max(tile_smem<T>(nb, 0), sizeof(double) * 8 * 512);
+  const int ns = tile_stages<T>(nb, 0);
+  const size_t sm = std::max(tile_smem<T>(nb, 0, ns), sizeof(double) * 8 * 512);
   const int g = orth_grid(c, c->n, (const void*)k_tproj<T>, sm);
   k_tproj<T><<<g, 256, sm, c->stream>>>((int)c->n, (const T*)Qb, (size_t)c->n * 8, nb, (const T*)W,
-                                        c->partials, mask, DEV_FIELD(c->lz, DevLanczos, status, int));
+                                        c->partials, mask, DEV_FIELD(c->lz, DevLanczos, status, int), ns);
   return g;
 }
 
@@ -135,10 +154,11 @@ int Orth<T>::gram_xy(Ctx* c, const void* X, const void* Y) {
     if (g > 0) return g;
   }
   set_attrs<T>();
-  const size_t sm = std::max(tile_smem<T>(1, 0), sizeof(double) * 8 * 512);
+  const int ns = tile_stages<T>(1, 0);
+  const size_t sm = std::max(tile_smem<T>(1, 0, ns), sizeof(double) * 8 * 512);
   const int g = orth_grid(c, c->n, (const void*)k_tproj<T>, sm);
   k_tproj<T><<<g, 256, sm, c->stream>>>((int)c->n, (const T*)X, (size_t)c->n * 8, 1, (const T*)Y,
-                                        c->partials, nullptr, DEV_FIELD(c->lz, DevLanczos, status, int));
+                                        c->partials, nullptr, DEV_FIELD(c->lz, DevLanczos, status, int), ns);
   return g;
 }
 
@@ -154,10 +174,12 @@ int Orth<T>::update(Ctx* c, const void* Qb, int nb, void* W, const int* mask) {
   // 8 warps x 5 pairs x 32 x 4 floats; FP64 8 warps x (32 or 64) slots x 16 doubles
   const size_t red = sizeof(T) == 4 ? tc_red_bytes(5)
                                     : sizeof(double) * 8 * (4 * (nb + 1) <= 32 ? 32 : 64) * 16;
-  const size_t sm = std::max(tile_smem<T>(nb, 8 * 64), red);
+  const int ns = tile_stages<T>(nb, 8 * 64);
+  const size_t sm = std::max(tile_smem<T>(nb, 8 * 64, ns), red);
   const int g = orth_grid(c, c->n, (const void*)k_tupdate<T>, sm);
   k_tupdate<T><<<g, 256, sm, c->stream>>>((int)c->n, (const T*)Qb, (size_t)c->n * 8, nb, (T*)W,
-                                          c->red + RED_H, c->partials, mask, DEV_FIELD(c->lz, DevLanczos, status, int));
+                                          c->red + RED_H, c->partials, mask, DEV_FIELD(c->lz, DevLanczos, status, int),
+                                          ns);
   return g;
 }
 
@@ -167,10 +189,11 @@ void Orth<T>::finalize(Ctx* c, const void* Qb, int nb, const void* W, void* out,
   USBS_LAUNCH_B(c, USBS_KIND_REORTH_FINAL, mask ? 0.0 : 8.0 * sizeof(T) * c->n * (nb + 2));
   if (on_tc<T>(c) && tc_final(c, Qb, nb, W, out, mask, seed)) return;
   set_attrs<T>();
-  const size_t sm = tile_smem<T>(nb, 8 * 64 + 64);
+  const int ns = tile_stages<T>(nb, 8 * 64 + 64);
+  const size_t sm = tile_smem<T>(nb, 8 * 64 + 64, ns);
   k_tfinalize<T><<<orth_grid(c, c->n, (const void*)k_tfinalize<T>, sm), 256, sm, c->stream>>>(
       (int)c->n, (const T*)Qb, (size_t)c->n * 8, nb, (const T*)W, c->red + RED_H2, c->lz, (T*)out,
-      mask, seed, DEV_FIELD(c->lz, DevLanczos, status, int));
+      mask, seed, DEV_FIELD(c->lz, DevLanczos, status, int), ns);
 }
 
 template <typename T>
@@ -180,10 +203,12 @@ void Orth<T>::restart(Ctx* c, const void* Qb, int J, int nout, const double* Y, 
   if (on_tc<T>(c) && tc_restart(c, Qb, J, nout, Y, out, resid, resid_slot)) return;
   set_attrs<T>();
   // stages, then Y: J x 8 nout values (FP64), or (hi, lo) TF32 pairs (FP32), 8 bytes each
-  const size_t sm = sizeof(T) * (2 * (size_t)(J / 8) * BlockStride<T>::value) + 8 * (size_t)J * nout * 8;
+  const size_t ybytes = 8 * (size_t)J * nout * 8;
+  const int ns = pipe_stages(stage_bytes<T>(J / 8), ybytes);
+  const size_t sm = (size_t)ns * stage_bytes<T>(J / 8) + ybytes;
   k_trestart<T><<<orth_grid(c, c->n, (const void*)k_trestart<T>, sm), 256, sm, c->stream>>>(
       (int)c->n, (const T*)Qb, (size_t)c->n * 8, J / 8, nout, Y, (T*)out, (size_t)c->n * 8,
-      (const T*)resid, resid_slot, DEV_FIELD(c->lz, DevLanczos, status, int));
+      (const T*)resid, resid_slot, DEV_FIELD(c->lz, DevLanczos, status, int), ns);
 }
 
 template struct Orth<float>;
@@ -198,14 +223,14 @@ namespace {
 __global__ void k_selftest_tile_wait(const float* __restrict__ src, int deliver, int* status) {
   __shared__ __align__(128) float buf[256];
   __shared__ uint64_t tbar[2];
-  tiles_begin(tbar);
+  tiles_begin(tbar, 2);
   if (threadIdx.x == 0) {
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     mbar_expect_tx(&tbar[0], 1024u);
     if (deliver) bulk_g2s(buf, src, 1024u, &tbar[0]);
   }
   const bool ok = tile_wait_cta(&tbar[0], 0, status);
-  tiles_end(tbar, !ok, 0, 0, status);
+  tiles_end(tbar, 2, ok ? -1 : 0, 0, 1, 1);
 }
 }  // namespace
 

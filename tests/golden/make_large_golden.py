@@ -9,7 +9,7 @@ Calls only oracle/ and the input generators (paper_2312_11801_gb300.instances). 
                  (k = 8, rho = 0.01, no sketch): per-step f(y), <C,X>, tr X, lambda_max,
                  relative infeasibility, model value and descent flag;
   er6000_solve   a solve of MaxCut on an Erdos-Renyi graph, n = 6000, average degree 6,
-                 to both gates <= 1e-3 (rho = 0.1, at most 800 iterations).
+                 to both gates <= 1e-3 (rho = 0.03, at most 800 iterations).
 Usage: python tests/golden/make_large_golden.py [case ...]
 """
 import json
@@ -65,9 +65,9 @@ def traj_case(pname, steps=6):
             "seconds": time.time() - t0}
 
 
-def solve_case(pname, tol=1e-3, max_iters=800):
+def solve_case(pname, tol=1e-3, max_iters=800, rho=0.03):
     prob = PROBLEMS[pname]()
-    o = OU.USBSOracle(prob, k=8, rho=0.1)
+    o = OU.USBSOracle(prob, k=8, rho=rho)
     t0 = time.time()
 
     def progress(d):
@@ -76,7 +76,7 @@ def solve_case(pname, tol=1e-3, max_iters=800):
 
     hist = o.solve(tol=tol, max_iters=max_iters, callback=progress)
     last = hist[-1]
-    return {"problem": pname, "n": prob.n, "rho": 0.1, "tol": tol, "iters": len(hist),
+    return {"problem": pname, "n": prob.n, "rho": rho, "tol": tol, "iters": len(hist),
             "converged": bool(last["relgap"] <= tol and last["relinf"] <= tol),
             "objective": o.objective(), "dual_bound": o.dual_bound(),
             "cx_scaled": o.state.cx, "f_scaled": o.state.f_y, "relgap": last["relgap"],

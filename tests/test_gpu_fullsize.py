@@ -207,8 +207,8 @@ def test_step_trajectory_mixed_torus400(mods):
 
 def test_solve_mixed_er6000(mods):
     """A mixed-precision solve at n = 6000 to both gates <= 1e-3 against the oracle's
-    solve to 1e-4 (rho = 0.1): each dual bound lies above the other side's primal value
-    up to the two gaps, and the objectives agree within the sum of the gaps."""
+    solve to the same gates (rho = 0.03): each dual bound lies above the other side's primal
+    value up to the two gaps, and the objectives agree within the sum of the gaps."""
     torch, U = mods
     g = _golden("er6000_solve")
     prob = _PROBLEMS[g["problem"]]()
