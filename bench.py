@@ -568,7 +568,7 @@ def run_c1(args, world, rank, local, pg):
     torch.cuda.set_device(local)
     prob = I.maxcut_er(800, 6.0, 0)
     stream = torch.cuda.Stream()
-    kw = dict(precision=U.PRECISION_FP64, rho=args.rho, max_iters=args.max_iters, stream=stream)
+    kw = dict(precision=U.PRECISION_FP64, rho=args.c1_rho, max_iters=args.max_iters, stream=stream)
     ctx = U.usbs_create(prob, **kw)
     for _ in range(args.warmup):
         U.usbs_solve(ctx, tol=TOL)
@@ -599,7 +599,7 @@ def run_c1(args, world, rank, local, pg):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "maxcut_er800_d6_s0_fp64_plain", "rho": args.rho, "tol": TOL, "k_c": 8,
+        "config": {"workload": "maxcut_er800_d6_s0_fp64_plain", "rho": args.c1_rho, "tol": TOL, "k_c": 8,
                    "iters_per_solve": [r["iters"] for r in res],
                    "converged": all(r["converged"] for r in res),
                    "objective": last["objective"], "dual_bound": last["dual_bound"]},
@@ -764,6 +764,7 @@ def main():
     ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "batched", "serve", "sweep"])
     ap.add_argument("--c3-n", type=int, default=65536)
     ap.add_argument("--c3-rho", type=float, default=0.01)
+    ap.add_argument("--c1-rho", type=float, default=0.1)
     ap.add_argument("--rho", type=float, default=0.03, help="rho of the batched, served and sweep workloads")
     ap.add_argument("--sweep-rhos", default="0.1,0.01", help="further rho values of the sweep, for (8, 0) and (7, 1)")
     ap.add_argument("--k-c", type=int, default=8, help="k_c of the batched and served workloads")

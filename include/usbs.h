@@ -34,9 +34,10 @@
 extern "C" {
 #endif
 
-#define USBS_ABI_VERSION 4   /* 2: usbs_eig_info.reruns, usbs_nystrom_round;
+#define USBS_ABI_VERSION 5   /* 2: usbs_eig_info.reruns, usbs_nystrom_round;
                                 3: certification of f(y) and the objective-relative gate;
-                                4: the App. B.1 model-value IPM, usbs_selftest_tile_wait */
+                                4: the App. B.1 model-value IPM, usbs_selftest_tile_wait;
+                                5: usbs_selftest_tf32_round */
 
 /* status codes */
 #define USBS_OK          0
@@ -347,6 +348,17 @@ long long usbs_launch_count(const usbs_ctx* ctx);
  * no counterpart: this checks the failure path of the library's own waits without a fault.
  */
 int usbs_selftest_tile_wait(int deliver);
+
+/*
+ * usbs_selftest_tf32_round -- the TF32 rounding of the FP32 Gram-Schmidt tiles (each
+ * operand is split into a TF32 high part and a TF32 low part before its m16n8k8 MMAs),
+ * run on the current device for `count` values x (host, FP32): ours[i] receives the bits of
+ * the tiles' rounding of x[i], ref[i] those of the PTX conversion cvt.rna.tf32.f32 (round to
+ * nearest, ties away from zero).  All three arrays are host memory of `count` elements,
+ * owned by the caller.  count = 0 is a no-op.  Returns USBS_OK, USBS_EINVAL (count < 0 or a
+ * NULL array with count > 0), USBS_ENOMEM or USBS_ECUDA.
+ */
+int usbs_selftest_tf32_round(int64_t count, const float* x, uint32_t* ours, uint32_t* ref);
 
 /*
  * usbs_sketch_update_static -- the sketch update of usbs_op_sketch_update,

@@ -203,7 +203,17 @@ __device__ __forceinline__ void tiles_end(uint64_t* bar, int ns, int it_abort, i
 // a0 (g, t), a1 (g+8, t), a2 (g, t+4), a3 (g+8, t+4); B (8 x 8) b0 (t, g), b1 (t+4, g);
 // C/D (16 x 8) c0 (g, 2t), c1 (g, 2t+1), c2 (g+8, 2t), c3 (g+8, 2t+1).
 // =============================================================================================
+// x rounded to TF32 (1 sign, 8 exponent, 10 mantissa bits), to nearest with ties away from
+// zero: half a unit of the 13 dropped bits is added to the sign-magnitude bit pattern (a
+// carry moves into the exponent exactly as rounding up does) and the 13 bits are cleared.
+// Two integer operations; for finite x the bits equal cvt.rna.tf32.f32's
+// (tests/test_gpu_kernels.py checks it against that instruction), which the tiles called
+// once per operand and which cost more issue slots.  Overflow gives inf; a NaN whose
+// payload lies in the dropped bits alone would come out as inf (the tiles see finite data).
 __device__ __forceinline__ uint32_t tf32_of(float x) {
+  return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u;
+}
+__device__ __forceinline__ uint32_t tf32_of_cvt(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
   return r;

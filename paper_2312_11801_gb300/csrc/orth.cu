@@ -232,6 +232,15 @@ __global__ void k_selftest_tile_wait(const float* __restrict__ src, int deliver,
   const bool ok = tile_wait_cta(&tbar[0], 0, status);
   tiles_end(tbar, 2, ok ? -1 : 0, 0, 1, 1);
 }
+
+// the tiles' TF32 rounding and the PTX conversion, side by side
+__global__ void k_selftest_tf32(int64_t count, const float* __restrict__ x, uint32_t* __restrict__ ours,
+                                uint32_t* __restrict__ ref) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    ours[i] = tf32_of(x[i]);
+    ref[i] = tf32_of_cvt(x[i]);
+  }
+}
 }  // namespace
 
 }  // namespace usbs
@@ -261,4 +270,33 @@ extern "C" int usbs_selftest_tile_wait(int deliver) {
     return USBS_ECUDA;
   }
   return status == USBS_ETIMEOUT ? USBS_ETIMEOUT : USBS_OK;
+}
+
+extern "C" int usbs_selftest_tf32_round(int64_t count, const float* x, uint32_t* ours, uint32_t* ref) {
+  using namespace usbs;
+  if (count < 0 || (count > 0 && (!x || !ours || !ref))) return USBS_EINVAL;
+  if (count == 0) return USBS_OK;
+  float* dx = nullptr;
+  uint32_t* dout = nullptr;
+  if (cudaMalloc(&dx, sizeof(float) * count) != cudaSuccess ||
+      cudaMalloc(&dout, sizeof(uint32_t) * 2 * count) != cudaSuccess) {
+    cudaGetLastError();
+    if (dx) cudaFree(dx);
+    return USBS_ENOMEM;
+  }
+  cudaError_t e = cudaMemcpy(dx, x, sizeof(float) * count, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    const int64_t blocks = std::min<int64_t>((count + 255) / 256, 4096);
+    k_selftest_tf32<<<(int)blocks, 256>>>(count, dx, dout, dout + count);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(ours, dout, sizeof(uint32_t) * count, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(ref, dout + count, sizeof(uint32_t) * count, cudaMemcpyDeviceToHost);
+  cudaFree(dx);
+  cudaFree(dout);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return USBS_ECUDA;
+  }
+  return USBS_OK;
 }

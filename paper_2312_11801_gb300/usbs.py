@@ -129,6 +129,7 @@ SIGNATURES = [
     ("usbs_kernel_stats", ctypes.c_int, [_P, ctypes.c_int, _D, ctypes.POINTER(ctypes.c_longlong), _D]),
     ("usbs_launch_count", ctypes.c_longlong, [_P]),
     ("usbs_selftest_tile_wait", ctypes.c_int, [ctypes.c_int]),
+    ("usbs_selftest_tf32_round", ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("usbs_instance_bytes", ctypes.c_uint64, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                               ctypes.c_int64, ctypes.c_int, ctypes.c_int]),
     ("usbs_server_params_default", None, [ctypes.POINTER(usbs_server_params)]),
@@ -421,6 +422,16 @@ def usbs_launch_count(ctx):
 def usbs_selftest_tile_wait(deliver):
     """The staged tiles' bounded wait run alone; returns the status code (no exception)."""
     return load().usbs_selftest_tile_wait(int(bool(deliver)))
+
+
+def usbs_selftest_tf32_round(x):
+    """The FP32 tiles' TF32 rounding of x and cvt.rna.tf32.f32's, as uint32 bit arrays."""
+    x = np.ascontiguousarray(x, np.float32)
+    ours = np.zeros(x.size, np.uint32)
+    ref = np.zeros(x.size, np.uint32)
+    _check(load().usbs_selftest_tf32_round(x.size, _ptr(x, ctypes.c_float), _ptr(ours, ctypes.c_uint32),
+                                           _ptr(ref, ctypes.c_uint32)), None)
+    return ours, ref
 
 
 def usbs_sketch_update_static(n, r, V_dev, S_dev, Psi_dev, P_dev, eta, stream=None):

@@ -47,7 +47,7 @@ def test_param_defaults_and_version(U):
     assert p.rho == 0.01 and p.beta == 0.25 and p.k_c == 8 and p.k_p == 0
     assert p.lanczos_restarts == 10 and p.ipm_mu_tol == 1e-7 and p.max_alt == 50
     assert p.certify_restarts == 0 and p.obj_gap_tol == 0.0 and p.model_value_ipm == 0
-    assert U.load().usbs_abi_version() == 4
+    assert U.load().usbs_abi_version() == 5
 
 
 def _expect_einval(U, prob, match, **kw):

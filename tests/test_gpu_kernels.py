@@ -125,3 +125,29 @@ def test_extreme_eigs(mods, case, ywhich, precision):
     res = np.linalg.norm(M @ evecs - evecs * evals, axis=0)
     assert res.max() <= (1e-8 if precision == 0 else 3e-5) * normM
     np.testing.assert_allclose(evecs.T @ evecs, np.eye(8), atol=1e-9 if precision == 0 else 2e-5)
+
+
+def test_tf32_rounding_matches_the_ptx_conversion(mods):
+    """The FP32 tiles split every operand into TF32 high and low parts; their rounding (two
+    integer operations on the bit pattern) must give the bits of cvt.rna.tf32.f32 (nearest,
+    ties away from zero) for finite normal inputs and zeros: random bit patterns over the
+    normal exponent range, values with exact ties (dropped bits 0x1000), ties one bit off
+    either way, values whose rounding carries into the exponent, and +-0."""
+    torch, U = mods
+    rng = np.random.default_rng(3)
+    sign = rng.integers(0, 2, 200_000, dtype=np.uint32) << 31
+    expo = rng.integers(1, 254, 200_000, dtype=np.uint32) << 23
+    mant = rng.integers(0, 1 << 23, 200_000, dtype=np.uint32)
+    bits = sign | expo | mant
+    ties = (bits & ~np.uint32(0x1FFF)) | np.uint32(0x1000)
+    near = np.concatenate([ties - np.uint32(1), ties + np.uint32(1)])
+    carry = (sign[:1000] | expo[:1000] | np.uint32(0x7FF000))
+    allb = np.concatenate([bits, ties, near, carry, np.array([0, 0x80000000], np.uint32)])
+    x = allb.view(np.float32)
+    ours, ref = U.usbs_selftest_tf32_round(x)
+    bad = np.nonzero(ours != ref)[0]
+    assert bad.size == 0, [(hex(allb[i]), hex(ours[i]), hex(ref[i])) for i in bad[:5]]
+    # the high part keeps 10 mantissa bits and is within half a TF32 unit of x
+    hi = ours.view(np.float32).astype(np.float64)
+    assert np.all((ours & np.uint32(0x1FFF)) == 0)
+    assert np.all(np.abs(hi - x) <= np.abs(x) * 2.0 ** -11 * (1 + 1e-12))
