@@ -202,6 +202,9 @@ __device__ __forceinline__ void tiles_end(uint64_t* bar, int ns, int it_abort, i
 // Fragment layout of m16n8k8 (g = lane / 4, t = lane % 4): A (16 x 8, row-major)
 // a0 (g, t), a1 (g+8, t), a2 (g, t+4), a3 (g+8, t+4); B (8 x 8) b0 (t, g), b1 (t+4, g);
 // C/D (16 x 8) c0 (g, 2t), c1 (g, 2t+1), c2 (g+8, 2t), c3 (g+8, 2t+1).
+// The projection, update and finalize bodies take the number of basis blocks NB (0..8) as a
+// template argument (the k_t*_dev bodies dispatch on it): every block loop is then unrolled
+// without run-time guards, which takes about a tenth of the update's instructions off.
 // =============================================================================================
 // x rounded to TF32 (1 sign, 8 exponent, 10 mantissa bits), to nearest with ties away from
 // zero: half a unit of the 13 dropped bits is added to the sign-magnitude bit pattern (a
@@ -264,7 +267,8 @@ __device__ __forceinline__ int dfrag_reg(int m, int c) { return ((m >> 3) << 1) 
 // Sums of X_i^T Y over the tile's rows for the blocks of `blocks` (block i at stage
 // offset i * BS; block nblk-1 may be Y itself), accumulated per block pair in acc: pair p
 // covers blocks 2p and 2p+1 (rows m 0..7 and 8..15 of the MMA).  Warp w takes the 8-row
-// k-steps w and w + 8 of the 128-row tile.
+// k-steps 2w and 2w + 1 of the 128-row tile: rows 16w .. 16w + 15, the rows it owns in the
+// row-wise products (X = W - Q H), so the update needs no CTA barrier between the two.
 template <int MAXP>
 __device__ __forceinline__ void tc_accum_xty(const float* st, int nblk, const float* Y, int warp, int g, int t,
                                              float (&accs)[MAXP][4], float (&accb)[MAXP][4]) {
@@ -272,7 +276,7 @@ __device__ __forceinline__ void tc_accum_xty(const float* st, int nblk, const fl
   const int off = t * 8 + g;   // element (row t, column g) of an 8-row step; + 32 for row t + 4
 #pragma unroll
   for (int kk = 0; kk < 2; ++kk) {
-    const int r0 = (warp + 8 * kk) * 8;
+    const int r0 = (2 * warp + kk) * 8;
     const float* y = Y + r0 * 8 + off;
     const SplitB b = split_b(y[0], y[32]);
 #pragma unroll
@@ -311,8 +315,10 @@ __device__ __forceinline__ void tc_reduce_xty(const float (&acc)[MAXP][4], int n
 }
 
 // H = Q^T W for nb <= 8 blocks
+template <int NB>
 __device__ __forceinline__ void tc_tproj(const int cta, const int ncta, int n, const float* Q, size_t bstride,
-                                         int nb, const float* W, double* partials, int* status, int ns = 2) {
+                                         const float* W, double* partials, int* status, int ns) {
+  constexpr int nb = NB;
   constexpr int TR = 128, BS = BlockStride<float>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* stages = reinterpret_cast<float*>(smem_raw);
@@ -354,8 +360,10 @@ __device__ __forceinline__ void tc_tproj(const int cta, const int ncta, int n, c
 
 // X = W - Q H (W overwritten, in shared memory and in global memory); then H2 = Q^T X and
 // G = X^T X.  H in Hs (nb x 64, FP32).
+template <int NB>
 __device__ __forceinline__ void tc_tupdate(const int cta, const int ncta, int n, const float* Q, size_t bstride,
-                                           int nb, float* W, const double* Hred, double* partials, int* status, int ns = 2) {
+                                           float* W, const double* Hred, double* partials, int* status, int ns) {
+  constexpr int nb = NB;
   constexpr int TR = 128, BS = BlockStride<float>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* stages = reinterpret_cast<float*>(smem_raw);
@@ -415,7 +423,8 @@ __device__ __forceinline__ void tc_tupdate(const int cta, const int ncta, int n,
       if (row0 < n) *reinterpret_cast<float2*>(W + (size_t)8 * row0 + 2 * t) = make_float2(v0, v1);
       if (row1 < n) *reinterpret_cast<float2*>(W + (size_t)8 * row1 + 2 * t) = make_float2(v2, v3);
     }
-    __syncthreads();
+    // phase 2 reads the 16 rows of X this warp wrote in phase 1: a warp barrier suffices
+    __syncwarp();
     // phase 2: H2 = Q^T X and G = X^T X (X is block nb of the pair list; rows past n are 0)
     tc_accum_xty<5>(st, nb + 1, Xs, warp, g, t, acc, accb);
     __syncthreads();
@@ -431,9 +440,11 @@ __device__ __forceinline__ void tc_tupdate(const int cta, const int ncta, int n,
 }
 
 // out = (W - Q H2) R^-1, deficient columns replaced (1: random, 2: zero)
+template <int NB>
 __device__ __forceinline__ void tc_tfinalize(const int cta, const int ncta, int n, const float* Q, size_t bstride,
-                                             int nb, const float* W, const double* H2red, const DevLanczos* lz,
-                                             float* out, uint64_t seed, int* status, int ns = 2) {
+                                             const float* W, const double* H2red, const DevLanczos* lz,
+                                             float* out, uint64_t seed, int* status, int ns) {
+  constexpr int nb = NB;
   constexpr int TR = 128, BS = BlockStride<float>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* stages = reinterpret_cast<float*>(smem_raw);
@@ -508,9 +519,12 @@ __device__ __forceinline__ void tc_tfinalize(const int cta, const int ncta, int 
 
 // out[o] = Q[:, :J] Y[:, 8o : 8o + 8] for o < nout <= 4; the residual block copied to
 // out[resid_slot] when resid is given.  Ys: J x 8 nout split pairs in shared memory.
+// NBK / NOUT > 0 fix nbk / nout at compile time (0: taken from the arguments).
+template <int NBK, int NOUT>
 __device__ __forceinline__ void tc_trestart(const int cta, const int ncta, int n, const float* Q, size_t bstride,
-                                            int nbk, int nout, const double* Y, float* out, size_t ostride,
-                                            const float* resid, int resid_slot, int* status, int ns = 2) {
+                                            int nbk_rt, int nout_rt, const double* Y, float* out, size_t ostride,
+                                            const float* resid, int resid_slot, int* status, int ns) {
+  const int nbk = NBK > 0 ? NBK : nbk_rt, nout = NOUT > 0 ? NOUT : nout_rt;
   constexpr int TR = 128, BS = BlockStride<float>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* stages = reinterpret_cast<float*>(smem_raw);
@@ -547,6 +561,7 @@ __device__ __forceinline__ void tc_trestart(const int cta, const int ncta, int n
     for (int o = 0; o < 4; ++o)
 #pragma unroll
       for (int u = 0; u < 4; ++u) d[o][u] = e[o][u] = 0.f;
+#pragma unroll
     for (int b = 0; b < nbk; ++b) {
       const float* q = st + (size_t)b * BS + (size_t)rb * 8;
       uint32_t h0, h1, h2, h3, l0, l1, l2, l3;
@@ -627,7 +642,17 @@ __device__ __forceinline__ void k_tproj_dev(const int cta, const int ncta, int n
                                                const int* USBS_RESTRICT mask, int* status, int ns = 2) {
   if constexpr (sizeof(T) == 4) {
     if (mask && *mask == 0) return;
-    tc_tproj(cta, ncta, n, Q, bstride, nb, W, partials, status, ns);
+    switch (nb) {
+      case 0: tc_tproj<0>(cta, ncta, n, Q, bstride, W, partials, status, ns); break;
+      case 1: tc_tproj<1>(cta, ncta, n, Q, bstride, W, partials, status, ns); break;
+      case 2: tc_tproj<2>(cta, ncta, n, Q, bstride, W, partials, status, ns); break;
+      case 3: tc_tproj<3>(cta, ncta, n, Q, bstride, W, partials, status, ns); break;
+      case 4: tc_tproj<4>(cta, ncta, n, Q, bstride, W, partials, status, ns); break;
+      case 5: tc_tproj<5>(cta, ncta, n, Q, bstride, W, partials, status, ns); break;
+      case 6: tc_tproj<6>(cta, ncta, n, Q, bstride, W, partials, status, ns); break;
+      case 7: tc_tproj<7>(cta, ncta, n, Q, bstride, W, partials, status, ns); break;
+      default: tc_tproj<8>(cta, ncta, n, Q, bstride, W, partials, status, ns); break;
+    }
     return;
   }
   if (mask && *mask == 0) return;
@@ -688,7 +713,17 @@ __device__ __forceinline__ void k_tupdate_dev(const int cta, const int ncta, int
                                                  const int* USBS_RESTRICT mask, int* status, int ns = 2) {
   if constexpr (sizeof(T) == 4) {
     if (mask && *mask == 0) return;
-    tc_tupdate(cta, ncta, n, Q, bstride, nb, W, Hred, partials, status, ns);
+    switch (nb) {
+      case 0: tc_tupdate<0>(cta, ncta, n, Q, bstride, W, Hred, partials, status, ns); break;
+      case 1: tc_tupdate<1>(cta, ncta, n, Q, bstride, W, Hred, partials, status, ns); break;
+      case 2: tc_tupdate<2>(cta, ncta, n, Q, bstride, W, Hred, partials, status, ns); break;
+      case 3: tc_tupdate<3>(cta, ncta, n, Q, bstride, W, Hred, partials, status, ns); break;
+      case 4: tc_tupdate<4>(cta, ncta, n, Q, bstride, W, Hred, partials, status, ns); break;
+      case 5: tc_tupdate<5>(cta, ncta, n, Q, bstride, W, Hred, partials, status, ns); break;
+      case 6: tc_tupdate<6>(cta, ncta, n, Q, bstride, W, Hred, partials, status, ns); break;
+      case 7: tc_tupdate<7>(cta, ncta, n, Q, bstride, W, Hred, partials, status, ns); break;
+      default: tc_tupdate<8>(cta, ncta, n, Q, bstride, W, Hred, partials, status, ns); break;
+    }
     return;
   }
   if (mask && *mask == 0) return;
@@ -792,7 +827,17 @@ __device__ __forceinline__ void k_tfinalize_dev(const int cta, const int ncta, i
                                                    const int* USBS_RESTRICT mask, uint64_t seed, int* status, int ns = 2) {
   if constexpr (sizeof(T) == 4) {
     if (mask && *mask == 0) return;
-    tc_tfinalize(cta, ncta, n, Q, bstride, nb, W, H2red, lz, out, seed, status, ns);
+    switch (nb) {
+      case 0: tc_tfinalize<0>(cta, ncta, n, Q, bstride, W, H2red, lz, out, seed, status, ns); break;
+      case 1: tc_tfinalize<1>(cta, ncta, n, Q, bstride, W, H2red, lz, out, seed, status, ns); break;
+      case 2: tc_tfinalize<2>(cta, ncta, n, Q, bstride, W, H2red, lz, out, seed, status, ns); break;
+      case 3: tc_tfinalize<3>(cta, ncta, n, Q, bstride, W, H2red, lz, out, seed, status, ns); break;
+      case 4: tc_tfinalize<4>(cta, ncta, n, Q, bstride, W, H2red, lz, out, seed, status, ns); break;
+      case 5: tc_tfinalize<5>(cta, ncta, n, Q, bstride, W, H2red, lz, out, seed, status, ns); break;
+      case 6: tc_tfinalize<6>(cta, ncta, n, Q, bstride, W, H2red, lz, out, seed, status, ns); break;
+      case 7: tc_tfinalize<7>(cta, ncta, n, Q, bstride, W, H2red, lz, out, seed, status, ns); break;
+      default: tc_tfinalize<8>(cta, ncta, n, Q, bstride, W, H2red, lz, out, seed, status, ns); break;
+    }
     return;
   }
   if (mask && *mask == 0) return;
@@ -875,7 +920,13 @@ __device__ __forceinline__ void k_trestart_dev(const int cta, const int ncta, in
                                                   T* USBS_RESTRICT out, size_t ostride,
                                                   const T* USBS_RESTRICT resid, int resid_slot, int* status, int ns = 2) {
   if constexpr (sizeof(T) == 4) {
-    tc_trestart(cta, ncta, n, Q, bstride, nbk, nout, Y, out, ostride, resid, resid_slot, status, ns);
+    // the shapes of the 16-, 32- and 64-column bases (restart: keep = J / 2; final: 1 block)
+    const int shape = nbk * 8 + nout;
+    if (shape == 4 * 8 + 2) tc_trestart<4, 2>(cta, ncta, n, Q, bstride, nbk, nout, Y, out, ostride, resid, resid_slot, status, ns);
+    else if (shape == 4 * 8 + 1) tc_trestart<4, 1>(cta, ncta, n, Q, bstride, nbk, nout, Y, out, ostride, resid, resid_slot, status, ns);
+    else if (shape == 8 * 8 + 4) tc_trestart<8, 4>(cta, ncta, n, Q, bstride, nbk, nout, Y, out, ostride, resid, resid_slot, status, ns);
+    else if (shape == 8 * 8 + 1) tc_trestart<8, 1>(cta, ncta, n, Q, bstride, nbk, nout, Y, out, ostride, resid, resid_slot, status, ns);
+    else tc_trestart<0, 0>(cta, ncta, n, Q, bstride, nbk, nout, Y, out, ostride, resid, resid_slot, status, ns);
     return;
   }
   constexpr int TR = TileRows<T>::value;
