@@ -140,7 +140,7 @@ def max_over_ranks(pg, x):
 # ---------------------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle on a bounded sample
 # ---------------------------------------------------------------------------------------
-SAMPLE_SIDE = 72         # a 72 x 72 torus of the same family (n = 5,184, block Lanczos path)
+SAMPLE_SIDE = 200        # a 200 x 200 torus of the same family (n = 40,000, block Lanczos path)
 SAMPLE_ITERS = 2
 
 
@@ -148,10 +148,10 @@ def oracle_sample(gpu_iters_per_solve, budget_s=40.0):
     """Oracle seconds per USBS iteration on the sample, scaled to the full workload.
 
     The sample runs the oracle (as it stands: block Lanczos to a 1e-6 residual for
-    n > 4096, FP64 throughout) on a 72 x 72 torus with the same weights law and sketch
-    rank, for up to SAMPLE_ITERS iterations after its cold start.  Every step of an
-    iteration is linear in n for these graphs, so seconds per iteration are scaled by
-    1e6 / 5184; solves/sec divides by the iterations the GPU solve needed.
+    n > 4096, FP64 throughout) on a 200 x 200 torus with the same weights law and sketch
+    rank, for up to SAMPLE_ITERS iterations after its cold start (10-30 s of CPU work).
+    Every step of an iteration is linear in n for these graphs, so seconds per iteration
+    are scaled by 1e6 / 40,000; solves/sec divides by the iterations the GPU solve needed.
     """
     from paper_2312_11801_gb300 import instances as I
     from oracle.usbs import USBSOracle

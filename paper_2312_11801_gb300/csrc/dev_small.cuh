@@ -387,68 +387,144 @@ __device__ __forceinline__ void k_ritz_f32_dev(DevLanczos* lz, int kc, double to
     Vv[i * LD + j] = (i == j) ? 1.f : 0.f;
   }
   __syncthreads();
-  const float skip2 = (float)(jac_eps * 1e-2) * (float)(jac_eps * 1e-2);
-  const float eps2 = (float)jac_eps * (float)jac_eps;
   float* Ac = A0;
   float* An = A1;
-  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    float off = 0.f, tot = 0.f;
-    for (int t = tid; t < J * J; t += blockDim.x) {
-      const int i = t / J, j = t % J;
-      const float x = Ac[i * LD + j];
-      tot = fmaf(x, x, tot);
-      if (i != j) off = fmaf(x, x, off);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      off += __shfl_xor_sync(FULL, off, o);
-      tot += __shfl_xor_sync(FULL, tot, o);
-    }
-    if (lane == 0) { wsum[0][warp] = off; wsum[1][warp] = tot; }
-    __syncthreads();
-    // every thread sums the warps' parts in the same order: one decision, no second barrier
-    float o2 = 0.f, t2 = 0.f;
-    for (int w = 0; w < nw; ++w) { o2 += wsum[0][w]; t2 += wsum[1][w]; }
-    if (o2 <= eps2 * t2) break;
-    if (tid == 0) lz->sweeps += 1;
-    for (int round = 0; round < J - 1; ++round) {
-      // lane l: the rotation of pair l mod half, from the pivots of A_cur
-      const int kr = lane & (half - 1);
-      const int pa = jac_circle(kr, round, J), pb = jac_circle(J - 1 - kr, round, J);
-      const int pr = min(pa, pb), qr = max(pa, pb);
-      float cr, sr;
-      jac_rot_f32(Ac[pr * LD + pr], Ac[qr * LD + qr], Ac[pr * LD + qr], skip2, cr, sr);
-      const int pqr = pr | (qr << 8);
-      for (int t0 = warp * 32; t0 < NITEM; t0 += blockDim.x) {   // warp-uniform
-        const int t = t0 + lane;
-        if (t0 < NBLK) {
-          // 2 x 2 block (p1, q1) x (p2, q2): rows by rotation k1, columns by k2
-          const int k1 = t / half, k2 = t % half;
-          const float c1 = __shfl_sync(FULL, cr, k1), s1 = __shfl_sync(FULL, sr, k1);
-          const float c2 = __shfl_sync(FULL, cr, k2), s2 = __shfl_sync(FULL, sr, k2);
-          const int pq1 = __shfl_sync(FULL, pqr, k1), pq2 = __shfl_sync(FULL, pqr, k2);
-          const int p1 = pq1 & 255, q1 = pq1 >> 8, p2 = pq2 & 255, q2 = pq2 >> 8;
-          const float a = Ac[p1 * LD + p2], b = Ac[p1 * LD + q2];
-          const float cc = Ac[q1 * LD + p2], d = Ac[q1 * LD + q2];
-          const float ra = c1 * a - s1 * cc, rb = c1 * b - s1 * d;
-          const float rc = s1 * a + c1 * cc, rd = s1 * b + c1 * d;
-          An[p1 * LD + p2] = c2 * ra - s2 * rb;
-          An[p1 * LD + q2] = s2 * ra + c2 * rb;
-          An[q1 * LD + p2] = c2 * rc - s2 * rd;
-          An[q1 * LD + q2] = s2 * rc + c2 * rd;
-        } else {
-          // V <- V G on row `row`, pair k (each (row, k) owned by one thread: in place)
-          const int u = t - NBLK;
-          const int k = u / J, row = u % J;
-          const float c = __shfl_sync(FULL, cr, k), sv = __shfl_sync(FULL, sr, k);
-          const int pq = __shfl_sync(FULL, pqr, k);
-          const int p = pq & 255, q = pq >> 8;
-          const float vp = Vv[row * LD + p], vq = Vv[row * LD + q];
-          Vv[row * LD + p] = c * vp - sv * vq;
-          Vv[row * LD + q] = sv * vp + c * vq;
-        }
+  if constexpr (J == 32) {
+    // One-sided (Hestenes) Jacobi by warp 0 with every column in registers: lane l holds
+    // column l of M = A + sigma I (sigma = 1.0625 ||A||_F makes M positive definite, so its
+    // eigenvalues lambda + sigma are distinct wherever A's are) and column l of V.  Round
+    // r = 1..31 pairs lane l with lane l ^ r (31 rounds meet every pair once: a sweep) and
+    // rotates the two columns of M to orthogonality, V alongside; the two lanes of a pair
+    // form the same Gram entries bit for bit (same products, same order), so they agree on
+    // the rotation.  At convergence M_0 V has orthogonal columns, V holds the eigenvectors
+    // and column l of M_0 V has norm lambda_l + sigma.  No shared memory and no barrier
+    // inside the sweeps; a sweep in which no pair rotates ends the iteration.
+    if (warp == 0) {
+      float fro = 0.f;
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const float x = A0[i * LD + lane];
+        fro = fmaf(x, x, fro);
       }
+      for (int o = 16; o > 0; o >>= 1) fro += __shfl_xor_sync(FULL, fro, o);
+      const float sigma = 1.0625f * sqrtf(fro) + 1e-30f;
+      float m[32], v[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        m[i] = A0[i * LD + lane] + (i == lane ? sigma : 0.f);
+        v[i] = (i == lane) ? 1.f : 0.f;
+      }
+      const float eps = (float)jac_eps;
+      for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        bool rotated = false;
+        for (int r = 1; r < 32; ++r) {
+          float pm[32];
+          float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f, g0 = 0.f, g1 = 0.f;
+#pragma unroll
+          for (int i = 0; i < 32; ++i) pm[i] = __shfl_xor_sync(FULL, m[i], r);
+#pragma unroll
+          for (int i = 0; i < 32; i += 2) {
+            a0 = fmaf(m[i], m[i], a0);
+            a1 = fmaf(m[i + 1], m[i + 1], a1);
+            b0 = fmaf(pm[i], pm[i], b0);
+            b1 = fmaf(pm[i + 1], pm[i + 1], b1);
+            g0 = fmaf(m[i], pm[i], g0);
+            g1 = fmaf(m[i + 1], pm[i + 1], g1);
+          }
+          const bool lo = lane < (lane ^ r);
+          const float own = a0 + a1, other = b0 + b1, g = g0 + g1;
+          const float al = lo ? own : other, be = lo ? other : own;   // |m_p|^2, |m_q|^2, p < q
+          float c = 1.f, sn = 0.f;
+          if (g != 0.f && fabsf(g) > eps * sqrtf(al * be)) {
+            const float zeta = (be - al) / (2.f * g);
+            const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+            c = 1.f / sqrtf(fmaf(t, t, 1.f));
+            sn = t * c;
+            rotated = true;
+          }
+          // p: c m_p - s m_q;  q: s m_p + c m_q
+          const float sq = lo ? -sn : sn;
+#pragma unroll
+          for (int i = 0; i < 32; ++i) m[i] = fmaf(sq, pm[i], c * m[i]);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const float pv = __shfl_xor_sync(FULL, v[i], r);
+            v[i] = fmaf(sq, pv, c * v[i]);
+          }
+        }
+        if (lane == 0) lz->sweeps += 1;
+        if (!__any_sync(FULL, rotated)) break;
+      }
+      float nn = 0.f;
+#pragma unroll
+      for (int i = 0; i < 32; ++i) nn = fmaf(m[i], m[i], nn);
+      A0[lane * LD + lane] = sqrtf(nn) - sigma;
+#pragma unroll
+      for (int i = 0; i < 32; ++i) Vv[i * LD + lane] = v[i];
+    }
+    __syncthreads();
+  } else {
+    const float skip2 = (float)(jac_eps * 1e-2) * (float)(jac_eps * 1e-2);
+    const float eps2 = (float)jac_eps * (float)jac_eps;
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+      float off = 0.f, tot = 0.f;
+      for (int t = tid; t < J * J; t += blockDim.x) {
+        const int i = t / J, j = t % J;
+        const float x = Ac[i * LD + j];
+        tot = fmaf(x, x, tot);
+        if (i != j) off = fmaf(x, x, off);
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        off += __shfl_xor_sync(FULL, off, o);
+        tot += __shfl_xor_sync(FULL, tot, o);
+      }
+      if (lane == 0) { wsum[0][warp] = off; wsum[1][warp] = tot; }
       __syncthreads();
-      float* tmp = Ac; Ac = An; An = tmp;
+      // every thread sums the warps' parts in the same order: one decision, no second barrier
+      float o2 = 0.f, t2 = 0.f;
+      for (int w = 0; w < nw; ++w) { o2 += wsum[0][w]; t2 += wsum[1][w]; }
+      if (o2 <= eps2 * t2) break;
+      if (tid == 0) lz->sweeps += 1;
+      for (int round = 0; round < J - 1; ++round) {
+        // lane l: the rotation of pair l mod half, from the pivots of A_cur
+        const int kr = lane & (half - 1);
+        const int pa = jac_circle(kr, round, J), pb = jac_circle(J - 1 - kr, round, J);
+        const int pr = min(pa, pb), qr = max(pa, pb);
+        float cr, sr;
+        jac_rot_f32(Ac[pr * LD + pr], Ac[qr * LD + qr], Ac[pr * LD + qr], skip2, cr, sr);
+        const int pqr = pr | (qr << 8);
+        for (int t0 = warp * 32; t0 < NITEM; t0 += blockDim.x) {   // warp-uniform
+          const int t = t0 + lane;
+          if (t0 < NBLK) {
+            // 2 x 2 block (p1, q1) x (p2, q2): rows by rotation k1, columns by k2
+            const int k1 = t / half, k2 = t % half;
+            const float c1 = __shfl_sync(FULL, cr, k1), s1 = __shfl_sync(FULL, sr, k1);
+            const float c2 = __shfl_sync(FULL, cr, k2), s2 = __shfl_sync(FULL, sr, k2);
+            const int pq1 = __shfl_sync(FULL, pqr, k1), pq2 = __shfl_sync(FULL, pqr, k2);
+            const int p1 = pq1 & 255, q1 = pq1 >> 8, p2 = pq2 & 255, q2 = pq2 >> 8;
+            const float a = Ac[p1 * LD + p2], b = Ac[p1 * LD + q2];
+            const float cc = Ac[q1 * LD + p2], d = Ac[q1 * LD + q2];
+            const float ra = c1 * a - s1 * cc, rb = c1 * b - s1 * d;
+            const float rc = s1 * a + c1 * cc, rd = s1 * b + c1 * d;
+            An[p1 * LD + p2] = c2 * ra - s2 * rb;
+            An[p1 * LD + q2] = s2 * ra + c2 * rb;
+            An[q1 * LD + p2] = c2 * rc - s2 * rd;
+            An[q1 * LD + q2] = s2 * rc + c2 * rd;
+          } else {
+            // V <- V G on row `row`, pair k (each (row, k) owned by one thread: in place)
+            const int u = t - NBLK;
+            const int k = u / J, row = u % J;
+            const float c = __shfl_sync(FULL, cr, k), sv = __shfl_sync(FULL, sr, k);
+            const int pq = __shfl_sync(FULL, pqr, k);
+            const int p = pq & 255, q = pq >> 8;
+            const float vp = Vv[row * LD + p], vq = Vv[row * LD + q];
+            Vv[row * LD + p] = c * vp - sv * vq;
+            Vv[row * LD + q] = sv * vp + c * vq;
+          }
+        }
+        __syncthreads();
+        float* tmp = Ac; Ac = An; An = tmp;
+      }
     }
   }
   // descending order under a strict total order (value, then index)
